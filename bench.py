@@ -1,0 +1,366 @@
+"""Benchmark of the batched GF(256) encode (Eq. 2) on one GB300, plus the
+region multiply-accumulate against HBM bandwidth, the plain
+one-region-op-per-launch form, and the CPU oracle as the reference arm.
+
+Default workload: 4096 generations x N = 64 source packets x 1500 B,
+K = 64 coded packets each, coding matrices uniform over GF(256) minus 0
+(393 MB of source, larger than the 129 MB L2, so no flush is needed between
+steps).  A step encodes the whole batch in one persistent launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gf|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own
+GPU (generations are independent; no collective on the data path) and rank 0
+prints one JSON line with the whole-job throughput (max time over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GF(256) batched encode GB/s (coded output)"
+WORKLOAD = "uniform batched encode: 4096 generations x N=64 x 1500 B, K=64, GF(256)"
+N_GENS, N_SRC, N_CODED, LEN = 4096, 64, 64, 1500
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        sm_max = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows if r[0] > 0.5 * sm_max] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": sm_max, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / cpu baseline: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_encode_rate(batch, budget_s: float, max_gens: int | None = None):
+    """Times the oracle's encode on whole generations until `budget_s` has
+    passed; returns (coded-output GB/s, generations done)."""
+    import oracle
+    oracle.build()
+    done, t0 = 0, time.perf_counter()
+    n = batch.src.shape[0]
+    while True:
+        i = done % n
+        oracle.encode(8, batch.src[i], batch.coef[i])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_gens and done >= max_gens):
+            break
+    out_bytes = done * N_CODED * LEN
+    return out_bytes / el / 1e9, done, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1909_02871_gb300 import synth
+    batch = synth.uniform_batch(n_gens=16, index=1)
+    for _ in range(args.warmup):
+        oracle_encode_rate(batch, 0.0, max_gens=1)
+    vals = []
+    for _ in range(args.steps):
+        v, done, el = oracle_encode_rate(batch, 0.0, max_gens=2)
+        vals.append(v)
+    value = statistics.median(vals)
+    ms = 2 * N_CODED * LEN / (value * 1e9) * 1e3 * (N_GENS / 2)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "2 generations per step, extrapolated to 4096"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: 2 generations (64 x 64 x 1500 B) encoded by the C oracle, "
+                                       "one thread"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gf(args, rank, world, local_rank):
+    import torch
+
+    from paper_1909_02871_gb300 import gf, synth
+    from paper_1909_02871_gb300 import build as gbuild
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gbuild.build()
+    gf.load()
+    hbm_peak, bf16_peak, peak_kind = _peaks()
+
+    batch = synth.uniform_batch(index=0)
+    src_h = torch.from_numpy(batch.src).pin_memory()
+    coef_h = torch.from_numpy(batch.coef).pin_memory()
+    src = src_h.to(dev)
+    coef = coef_h.to(dev)
+    out = torch.empty((N_GENS, N_CODED, LEN), dtype=torch.uint8, device=dev)
+    gens = [(8, N_SRC, N_CODED, LEN, src[i], coef[i], out[i]) for i in range(N_GENS)]
+    path = {"auto": gf.PATH_AUTO, "table": gf.PATH_TABLE, "bitsliced": gf.PATH_BITSLICED}[args.path]
+    plan = gf.Plan.encode(gens, path=path)
+    chosen = gf.gf_autotune_query(8, N_SRC, N_CODED, LEN) if path == gf.PATH_AUTO else (path, 0)
+    stream = torch.cuda.Stream(device=dev)
+    launches_per_step = plan.kernel_count
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.launch(stream)
+    stream.synchronize()
+
+    # timed region: per-step events on the launching stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for s in range(args.steps):
+                plan.launch(stream)
+                ev[s + 1].record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    out_bytes = N_GENS * N_CODED * LEN
+    value = world * out_bytes * args.steps / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args.steps
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the step is one launch of it)
+    avg_ms = statistics.mean(step_ms)
+    if chosen[0] == gf.PATH_BITSLICED:
+        flops = 2.0 * (8 * N_CODED) * (8 * N_SRC) * LEN * N_GENS
+        peak = bf16_peak * 2.0  # FP8 dense = 2 x bf16 (nominal ratio)
+        roof = {"bound": "tensor", "achieved": flops / (avg_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "kernel": "encode_bitsliced_kernel", "peak_kind": f"{peak_kind} bf16 x 2 (fp8 nominal ratio)"}
+    else:
+        # 5 integer instructions (2 prmt + 3 lop3) per 4-byte word and coefficient
+        ops = 5.0 * (LEN / 4.0) * N_SRC * N_CODED * N_GENS
+        sm_mhz = clocks.get("sm_mhz") or 2070.0
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": ops / (avg_ms / 1e3) / 1e12, "peak": peak, "unit": "Tops/s",
+                "kernel": "encode_table_kernel",
+                "peak_kind": "derived: 152 SMs x 128 int32 lanes x median SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = args.traffic
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gens": N_GENS, "n_src": N_SRC, "n_coded": N_CODED, "len": LEN,
+                       "field": "GF(256)", "path": {0: "auto", 1: "table", 2: "bitsliced"}[chosen[0]],
+                       "l2": "inputs larger than L2 (393 MB source per step)",
+                       "parallelism": f"replicas x{world}"},
+            "p50_step_ms": statistics.median(step_ms),
+            "p99_step_ms": float(np.percentile(step_ms, 99)),
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks, "roofline": roof}
+
+    if rank == 0 and not args.quick:
+        line["source_GBps"] = value * N_SRC / N_CODED
+        line["region_madd"] = bench_region(gf, torch, dev, stream, hbm_peak, peak_kind)
+        line["plain"] = bench_plain(gf, torch, dev, stream, src, coef, out, value)
+        line["e2e"] = bench_e2e(gf, torch, dev, stream, src_h, coef_h, args, plan, src, coef, out)
+        v, done, el = oracle_encode_rate(batch, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{done} generations of the same batch (64 x 64 x 1500 B) encoded by the "
+                                          f"C oracle in {el:.1f} s, one thread"}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_region(gf, torch, dev, stream, hbm_peak, peak_kind):
+    """gf_region_madd / gf_region_mul on a 1 GiB region (larger than L2), GF(256)."""
+    n = 1 << 30
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    a = torch.randint(0, 256, (n,), dtype=torch.uint8, device=dev, generator=g)
+    b = torch.randint(0, 256, (n,), dtype=torch.uint8, device=dev, generator=g)
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, fn, bytes_per in (("madd", gf.gf_region_madd, 3), ("mul", gf.gf_region_mul, 2)):
+            for _ in range(3):
+                fn(8, b, a, 0x8E, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record(stream)
+            for _ in range(reps):
+                fn(8, b, a, 0x8E, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = bytes_per * n / (ms / 1e3) / 1e9
+            res[name] = {"GBps_hbm": gbs, "frac": gbs / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind,
+                         "ms": ms, "len": n}
+    del a, b
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_plain(gf, torch, dev, stream, src, coef, out, batched_value):
+    """The plain form: one region op per launch (K zero fills + K*N madds per
+    generation), timed on 4 generations and extrapolated to the batch."""
+    coef_h = coef[:4].cpu().numpy()
+    G = 4
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for gi in range(G):
+            for k in range(N_CODED):
+                dst = out[gi, k]
+                gf.gf_region_mul(8, dst, dst, 0, stream=stream)
+                for i in range(N_SRC):
+                    gf.gf_region_madd(8, dst, src[gi, i], int(coef_h[gi, k, i]), stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    ms = max(e0.elapsed_time(e1), wall * 1e3)
+    value = G * N_CODED * LEN / (ms / 1e3) / 1e9
+    return {"value": value, "unit": "GB/s", "launches": G * N_CODED * (N_SRC + 1),
+            "sample": f"{G} generations, extrapolated (rate is per generation)",
+            "batched_over_plain": batched_value / value}
+
+
+def bench_e2e(gf, torch, dev, stream, src_h, coef_h, args, plan, src, coef, out):
+    """Same metric through the public API with host buffers: pinned H2D of the
+    sources and coding matrices, the encode, D2H of the coded packets."""
+    out_h = torch.empty(out.shape, dtype=torch.uint8).pin_memory()
+    steps = max(3, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            src.copy_(src_h, non_blocking=True)
+            coef.copy_(coef_h, non_blocking=True)
+            plan.launch(stream)
+            out_h.copy_(out, non_blocking=True)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            src.copy_(src_h, non_blocking=True)
+            coef.copy_(coef_h, non_blocking=True)
+            plan.launch(stream)
+            out_h.copy_(out, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": N_GENS * N_CODED * LEN / (ms / 1e3) / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": int(src_h.numel() + coef_h.numel()), "d2h_bytes_per_step": int(out_h.numel()),
+            "ms_per_step": ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
+    ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "gf":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gf(args, rank, world, local_rank)
+    if world > 1 and args.impl == "gf":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * gf.h -- C ABI of the GB300 (sm_103a) GF(2^n) network-coding library.
+ *
+ * The operations follow the statement of the problem in section II of
+ * Guenther, Appel, Carle, "Galois Field Arithmetics for Linear Network Coding
+ * using AVX 512 Instruction Set Extensions" (arXiv:1909.02871):
+ *
+ *   - field GF(q), q = 2^n with n in {1, 2, 4, 8} (GF(2), GF(4), GF(16),
+ *     GF(256)); addition is XOR, multiplication the polynomial product
+ *     reduced by x^2+x+1, x^4+x+1 and x^8+x^4+x^3+x^2+1 respectively (the
+ *     paper fixes no polynomial; these are the library's reading);
+ *   - a packet of len bytes holds 8*len/n words; word j of a byte occupies
+ *     bits [j*n, (j+1)*n), bit i of a word is the coefficient of x^i
+ *     (GF(16) is nibble-packed, GF(4) holds four words per byte);
+ *   - coefficients (coding-vector entries) are stored one field element per
+ *     byte, valid iff < 2^n.
+ *
+ * Conventions of every entry point:
+ *   - pointers named dst/src/out/payload/coef are DEVICE pointers owned by
+ *     the caller, unless stated otherwise; descriptor arrays (gf_gen_t,
+ *     gf_dec_t) are HOST arrays that the call reads before it returns;
+ *   - all work is enqueued on `stream` (NULL = legacy default stream) and the
+ *     call returns without waiting for it, unless stated otherwise;
+ *   - the return value is a status: GF_OK (0) or a negative GF_E* code; a
+ *     call that returns an error has enqueued nothing;
+ *   - no call takes torch or other framework types.
+ */
+#ifndef GF_GB300_H
+#define GF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream; NULL is the legacy default stream. */
+typedef struct CUstream_st *gf_stream_t;
+
+/* Status codes. */
+#define GF_OK 0
+#define GF_EINVAL (-1)    /* bad field, coefficient >= 2^n, negative size, NULL pointer with len > 0 */
+#define GF_EOVERLAP (-2)  /* dst and src overlap without being identical */
+#define GF_ENOMEM (-3)    /* device or host allocation failed */
+#define GF_ERANK (-4)     /* a decode reached rank < n_src (reported by gf_decode_check) */
+#define GF_ETIMEOUT (-5)  /* a device-side wait gave up (reported by gf_device_status) */
+#define GF_ECUDA (-6)     /* a CUDA runtime call or kernel launch failed */
+#define GF_ENOTSUP (-7)   /* the requested path is not available on this device */
+
+/* Human-readable name of a status code (static string). */
+const char *gf_strerror(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int gf_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Region operations (section II: madd, b := b + c*a)                  */
+/* ------------------------------------------------------------------ */
+
+/*
+ * gf_region_madd: dst := dst + coef * src over GF(2^field), on every word of
+ * the len-byte regions (the madd operation of section II and of Algorithms 1
+ * and 2 of section IV; coef 0 is a no-op and coef 1 a plain XOR, the two
+ * trivial cases of section IV).
+ *   field  bits per word: 1, 2, 4 or 8
+ *   dst    device pointer, len bytes, read and written
+ *   src    device pointer, len bytes, read; may equal dst (then dst := (1+coef)*dst)
+ *   coef   field element, must be < 2^field
+ *   len    bytes, any value >= 0, any alignment (16-byte aligned regions with
+ *          equal alignment take the vector path)
+ * Errors: GF_EINVAL (field, coef, NULL with len > 0), GF_EOVERLAP (regions
+ * overlap without being identical), GF_ECUDA (launch failure).
+ */
+int gf_region_madd(int field, uint8_t *dst, const uint8_t *src, uint8_t coef, size_t len,
+                   gf_stream_t stream);
+
+/*
+ * gf_region_mul: dst := coef * src over GF(2^field) (coef 0 zero-fills,
+ * coef 1 copies).  Needed by decode to normalise a pivot row; the paper's
+ * madd with a zero accumulator.  Arguments and errors as gf_region_madd;
+ * dst == src multiplies in place.
+ */
+int gf_region_mul(int field, uint8_t *dst, const uint8_t *src, uint8_t coef, size_t len,
+                  gf_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Generation encode (section II, Eq. 1 and Eq. 2)                     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One generation to encode: the K = n_coded coded packets
+ *     out_k = sum_i coef[k][i] * src_i        (Eq. 2, one row of B per packet)
+ * of the N = n_src source packets (the columns of A in Eq. 1).
+ *   src   device, n_src packets of len bytes, packet i at src + i*len
+ *   coef  device, n_coded x n_src coefficients, row-major, one per byte
+ *   out   device, n_coded packets of len bytes, packet k at out + k*len;
+ *         written (not accumulated); must not overlap src or coef
+ */
+typedef struct gf_gen {
+    int32_t field;     /* 1, 2, 4 or 8 */
+    int32_t n_src;     /* N >= 0 */
+    int32_t n_coded;   /* K >= 0 */
+    int32_t reserved;  /* must be 0 */
+    uint64_t len;      /* bytes per packet */
+    const uint8_t *src;
+    const uint8_t *coef;
+    uint8_t *out;
+} gf_gen_t;
+
+/* Encode paths. */
+#define GF_PATH_AUTO 0       /* autotuned choice per shape bucket */
+#define GF_PATH_TABLE 1      /* per-coefficient split tables, prmt lookups, integer ALU */
+#define GF_PATH_BITSLICED 2  /* GF(256) only: 8x8 GF(2) bit matrices on FP8 tensor cores */
+
+/*
+ * gf_encode_batched: encode n_gens generations (uneven N, K, len and field
+ * allowed) in one persistent launch.  `gens` is a host array of n_gens
+ * descriptors, read before the call returns.  Coefficients >= 2^field are
+ * not detected here (they give unspecified output bytes but no fault); use
+ * gf_encode_validate to check them.  Errors: GF_EINVAL (a descriptor),
+ * GF_ENOMEM (library workspace), GF_ECUDA.
+ */
+int gf_encode_batched(const gf_gen_t *gens, int n_gens, gf_stream_t stream);
+
+/* As gf_encode_batched with an explicit path (GF_PATH_*).  GF_ENOTSUP if the
+ * path cannot run a generation of the batch (bit-sliced: GF(256) only). */
+int gf_encode_batched_ex(const gf_gen_t *gens, int n_gens, int path, gf_stream_t stream);
+
+/*
+ * gf_encode_validate: synchronously checks every coefficient of every
+ * generation against its field; returns GF_OK, GF_EINVAL or GF_ECUDA.
+ * Waits for `stream`.
+ */
+int gf_encode_validate(const gf_gen_t *gens, int n_gens, gf_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Decode (Gauss-Jordan elimination; the paper describes no decoder)   */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One generation to decode from n_recv received coded packets, in arrival
+ * order.  Rows are processed in order; each is reduced against the pivots
+ * found so far, dropped if it reduces to zero (not innovative), otherwise
+ * normalised and used to eliminate its pivot column from the other rows;
+ * processing stops when the rank reaches n_src.
+ *   coef     device, n_recv x n_src coding vectors, one element per byte
+ *   payload  device, n_recv packets of len bytes
+ *   out      device, n_src packets of len bytes: decoded source p, or zeros
+ *            if source p is not determined by the rows received
+ *   rank     device int32: rank reached (== n_src on success)
+ *   used     device int32 or NULL: received rows consumed
+ *   solved   device, n_src bytes or NULL: 1 where out row p is decoded
+ */
+typedef struct gf_dec {
+    int32_t field;
+    int32_t n_src;    /* N, 0 <= N <= 1024 */
+    int32_t n_recv;   /* R, 0 <= R <= 4096 */
+    int32_t reserved; /* must be 0 */
+    uint64_t len;
+    const uint8_t *coef;
+    const uint8_t *payload;
+    uint8_t *out;
+    int32_t *rank;
+    int32_t *used;
+    uint8_t *solved;
+} gf_dec_t;
+
+/*
+ * gf_decode_batched: decode n_gens generations.  Coefficient elimination runs
+ * one CTA per generation (warp-ballot pivot search, row operations as
+ * split-table region madds in shared memory); the payloads are then combined
+ * by the batched encode with the elimination's transform.  Uses library
+ * workspace (device memory, grown on demand).  Rank deficiency is not an
+ * error of this call: read `rank`, or call gf_decode_check.
+ * Errors: GF_EINVAL, GF_ENOMEM, GF_ECUDA.
+ */
+int gf_decode_batched(const gf_dec_t *gens, int n_gens, gf_stream_t stream);
+
+/* Waits for `stream`, then returns GF_ERANK if any generation of `gens`
+ * reached rank < n_src, else GF_OK (GF_ECUDA on a CUDA error). */
+int gf_decode_check(const gf_dec_t *gens, int n_gens, gf_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Plans: pre-uploaded batches for CUDA graph capture                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct gf_plan gf_plan_t;
+
+/*
+ * gf_encode_plan_create: uploads the descriptors and the tile work list of
+ * an encode batch into library-owned device memory and fixes the path
+ * (GF_PATH_AUTO consults the autotuner).  Synchronous.  The caller's device
+ * buffers must stay valid while the plan is used.
+ */
+int gf_encode_plan_create(const gf_gen_t *gens, int n_gens, int path, gf_plan_t **plan);
+
+/* gf_decode_plan_create: the same for a decode batch. */
+int gf_decode_plan_create(const gf_dec_t *gens, int n_gens, gf_plan_t **plan);
+
+/* gf_plan_launch: enqueues the plan's kernels on `stream` (no allocation, no
+ * host-device copy: safe inside stream capture). */
+int gf_plan_launch(gf_plan_t *plan, gf_stream_t stream);
+
+/* Number of kernel launches gf_plan_launch enqueues. */
+int gf_plan_kernel_count(const gf_plan_t *plan);
+
+/* Releases a plan (waits for the device first). NULL is ignored. */
+int gf_plan_destroy(gf_plan_t *plan);
+
+/* ------------------------------------------------------------------ */
+/* Autotuner (encode tile shapes and path per shape bucket)            */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A shape bucket is (field, ceil(log2 n_src), ceil(log2 n_coded),
+ * ceil(log2 len)).  gf_autotune_encode allocates n_gens generations of that
+ * shape (device memory, freed before it returns), times every candidate --
+ * the bit-sliced path where it applies and each table-path tile shape --
+ * on `stream`, and records the fastest for the bucket; GF_PATH_AUTO then uses
+ * it for every generation in the bucket.  Synchronous.  *path / *variant
+ * (may be NULL) receive the choice.  Errors: GF_EINVAL, GF_ENOMEM, GF_ECUDA.
+ */
+int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t len, int n_gens, gf_stream_t stream,
+                       int *path, int *variant);
+
+/* Record a choice for a bucket without timing (path GF_PATH_TABLE or
+ * GF_PATH_BITSLICED, variant 0..3 = table tile shape). */
+int gf_autotune_set(int field, int n_src, int n_coded, uint64_t len, int path, int variant);
+
+/* The choice GF_PATH_AUTO makes for a shape (recorded, else the heuristic). */
+int gf_autotune_query(int field, int n_src, int n_coded, uint64_t len, int *path, int *variant);
+
+/* Forget every recorded choice. */
+int gf_autotune_clear(void);
+
+/* Save / load recorded choices as text lines
+ * "field log2N log2K log2len path variant" (host file path). */
+int gf_autotune_save(const char *path);
+int gf_autotune_load(const char *path);
+
+/* ------------------------------------------------------------------ */
+/* Device status                                                       */
+/* ------------------------------------------------------------------ */
+
+/* Waits for the current device, returns and clears the library's device-side
+ * error word: GF_OK, or GF_ETIMEOUT if a bounded wait inside a kernel gave up. */
+int gf_device_status(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_GB300_H */

@@ -1,0 +1,165 @@
+"""GPU parity of the batched encode (Eq. 2) against the oracle (bit-exact),
+through the C ABI: single generation, ragged/uneven batches, every table
+tile shape, the bit-sliced tensor-core path, plans and CUDA graph replay,
+and the full 4096 x 64 x 1500 B batch on sampled generations."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_02871_gb300 import gf, synth
+
+from gpu_util import dev, to_dev, to_host, torch
+
+pytestmark = pytest.mark.gpu
+FIELDS = (1, 2, 4, 8)
+
+
+def _run(items, path=gf.PATH_AUTO):
+    """items: list of (field, src np N x L, coef np K x N) -> list of outputs."""
+    keep, gens, outs = [], [], []
+    for field, src, coef in items:
+        K, N = coef.shape
+        L = src.shape[1] if src.ndim == 2 else 0
+        s = to_dev(src.reshape(-1)) if src.size else torch.zeros(1, dtype=torch.uint8, device=dev())
+        c = to_dev(coef.reshape(-1)) if coef.size else torch.zeros(1, dtype=torch.uint8, device=dev())
+        o = torch.full((max(K * L, 1),), 0xA5, dtype=torch.uint8, device=dev())
+        keep += [s, c, o]
+        gens.append((field, N, K, L, s, c, o))
+        outs.append((o, K, L))
+    gf.gf_encode_batched(gens, path=path)
+    return [to_host(o)[:K * L].reshape(K, L) for o, K, L in outs]
+
+
+@pytest.mark.parametrize("field", FIELDS)
+def test_single_generation(field):
+    gen = synth.generation(field)
+    coef = gen.coef_stream[:gen.n_coded]
+    (out,) = _run([(field, gen.src, coef)])
+    assert np.array_equal(out, oracle.encode(field, gen.src, coef))
+
+
+def _ragged_items(seed, fields=FIELDS):
+    g = synth.choice(50, seed)
+    items = []
+    for N in (0, 1, 3, 17, 64):
+        for K in (0, 1, 15, 16, 17, 33):
+            L = int(g.choice([0, 1, 5, 127, 128, 129, 513, 1500, 4097]))
+            field = int(g.choice(fields))
+            src = synth.random_bytes(g, (N, L))
+            coef = synth.coefficients(g, field, (K, N), nonzero=False)
+            items.append((field, src, coef))
+    return items
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_ragged_uneven_batch_one_launch(seed):
+    items = _ragged_items(seed)
+    outs = _run(items)
+    for (field, src, coef), out in zip(items, outs):
+        assert np.array_equal(out, oracle.encode(field, src, coef)), (field, src.shape, coef.shape)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_table_tile_shape(variant):
+    items = [it for it in _ragged_items(7) if it[2].size and it[1].size]
+    try:
+        for field, src, coef in items:
+            gf.gf_autotune_set(field, src.shape[0], coef.shape[0], src.shape[1], gf.PATH_TABLE, variant)
+        outs = _run(items, path=gf.PATH_TABLE)
+    finally:
+        gf.gf_autotune_clear()
+    for (field, src, coef), out in zip(items, outs):
+        assert np.array_equal(out, oracle.encode(field, src, coef))
+
+
+def _bitsliced_ok():
+    try:
+        (o,) = _run([(8, np.zeros((32, 512), np.uint8), np.ones((32, 32), np.uint8))], path=gf.PATH_BITSLICED)
+        return True
+    except gf.GFError as e:
+        if e.status == gf.GF_ENOTSUP:
+            return False
+        raise
+
+
+def test_bitsliced_rejects_other_fields():
+    src = np.zeros((4, 64), np.uint8)
+    coef = np.ones((4, 4), np.uint8)
+    s, c, o = to_dev(src.reshape(-1)), to_dev(coef.reshape(-1)), torch.zeros(256, dtype=torch.uint8, device=dev())
+    assert gf.encode_status([(4, 4, 4, 64, s, c, o)], path=gf.PATH_BITSLICED) == gf.GF_ENOTSUP
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 1500), (16, 16, 1500), (1, 1, 1), (33, 70, 255), (128, 96, 4097),
+                                   (255, 300, 700), (64, 64, 256), (7, 200, 3000)])
+def test_bitsliced_vs_oracle(shape):
+    if not _bitsliced_ok():
+        pytest.skip("bit-sliced path unavailable")
+    N, K, L = shape
+    g = synth.choice(60, N, K, L)
+    src = synth.random_bytes(g, (N, L))
+    coef = synth.coefficients(g, 8, (K, N), nonzero=False)
+    (out,) = _run([(8, src, coef)], path=gf.PATH_BITSLICED)
+    assert np.array_equal(out, oracle.encode(8, src, coef))
+
+
+def test_bitsliced_equals_table_on_batch():
+    if not _bitsliced_ok():
+        pytest.skip("bit-sliced path unavailable")
+    b = synth.uniform_batch(n_gens=24, index=3)
+    items = [(8, b.src[i], b.coef[i]) for i in range(24)]
+    a = _run(items, path=gf.PATH_BITSLICED)
+    t = _run(items, path=gf.PATH_TABLE)
+    for x, y in zip(a, t):
+        assert np.array_equal(x, y)
+    for i in (0, 23):
+        assert np.array_equal(a[i], oracle.encode(8, b.src[i], b.coef[i]))
+
+
+def test_plan_and_graph_replay():
+    items = _ragged_items(3)
+    keep, gens, outs = [], [], []
+    for field, src, coef in items:
+        K, N = coef.shape
+        L = src.shape[1]
+        s = to_dev(src.reshape(-1)) if src.size else torch.zeros(1, dtype=torch.uint8, device=dev())
+        c = to_dev(coef.reshape(-1)) if coef.size else torch.zeros(1, dtype=torch.uint8, device=dev())
+        o = torch.zeros(max(K * L, 1), dtype=torch.uint8, device=dev())
+        keep += [s, c, o]
+        gens.append((field, N, K, L, s, c, o))
+        outs.append((o, K, L))
+    plan = gf.Plan.encode(gens)
+    assert plan.kernel_count >= 1
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        plan.launch(stream)  # warm-up outside capture
+        stream.synchronize()
+        for o, _, _ in outs:
+            o.zero_()
+        with torch.cuda.graph(graph, stream=stream):
+            plan.launch(stream)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    for (field, src, coef), (o, K, L) in zip(items, outs):
+        assert np.array_equal(to_host(o)[:K * L].reshape(K, L), oracle.encode(field, src, coef))
+    plan.close()
+
+
+def test_full_uniform_batch_sampled():
+    """The 4096 x (N=64 x 1500 B) GF(256) batch, K = 64, in the launch the
+    benchmark times (path chosen by the autotuner); sampled generations are
+    compared with the oracle."""
+    b = synth.uniform_batch()
+    G, N, L = b.src.shape
+    K = b.coef.shape[1]
+    src = to_dev(b.src)
+    coef = to_dev(b.coef)
+    out = torch.empty((G, K, L), dtype=torch.uint8, device=dev())
+    gens = [(8, N, K, L, src[i], coef[i], out[i]) for i in range(G)]
+    for path in (gf.PATH_AUTO, gf.PATH_TABLE):
+        out.fill_(0)
+        gf.gf_encode_batched(gens, path=path)
+        torch.cuda.synchronize()
+        for i in (0, 1, 2047, 4095):
+            assert np.array_equal(out[i].cpu().numpy(), oracle.encode(8, b.src[i], b.coef[i])), (path, i)
