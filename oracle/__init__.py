@@ -169,7 +169,10 @@ def decode(n: int, coef: np.ndarray, payload: np.ndarray, n_src: int | None = No
     R, N = coef.shape
     if n_src is not None:
         assert n_src == N
-    payload = np.ascontiguousarray(payload, dtype=np.uint8).reshape(R, -1)
+    payload = np.ascontiguousarray(payload, dtype=np.uint8)
+    if payload.ndim != 2:
+        payload = payload.reshape(R, -1)
+    assert payload.shape[0] == R
     L = payload.shape[1]
     _check_field(n)
     out = np.zeros((N, L), dtype=np.uint8)

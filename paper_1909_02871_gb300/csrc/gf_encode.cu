@@ -319,6 +319,8 @@ int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBa
             if (g.field != 8 || !bitsliced_available()) {
                 if (path == GF_PATH_BITSLICED) return GF_ENOTSUP;
                 p = GF_PATH_TABLE;
+            } else if (!bitsliced_supports(g)) {
+                p = GF_PATH_TABLE;
             }
         }
         if (p == GF_PATH_BITSLICED) {

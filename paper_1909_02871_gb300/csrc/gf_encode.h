@@ -66,6 +66,10 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len);
 // Whether the bit-sliced (tcgen05) path can run on the current device.
 bool bitsliced_available();
 
+// Whether a generation fits the bit-sliced kernel (GF(256), 1 <= N <= 128,
+// K >= 1, len >= 1); others of a bit-sliced batch run on the table path.
+bool bitsliced_supports(const EncGen &g);
+
 // Split `gens` into per-path batches according to `path` (GF_PATH_*).
 // Returns GF_OK, GF_EINVAL or GF_ENOTSUP.
 int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBatch> &out);
