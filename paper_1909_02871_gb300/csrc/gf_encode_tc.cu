@@ -16,14 +16,17 @@
 //     byte position, 4 FP8 elements per column), no shared-memory traffic;
 //   B (K = 8N x N = 128 output bits of 16 coded packets): the coefficients'
 //     bit matrices as FP8 0/1, K-major, 128-byte swizzled, resident in shared
-//     memory for the whole work item, copied from a 16 KB per-CTA table of
-//     the 256 possible 8x8 blocks;
+//     memory for the whole work item (N <= 64: 64 KB), copied from a 16 KB
+//     per-CTA table of the 256 possible 8x8 blocks;
 //   D (128 lanes x 128 FP32 columns), double-buffered in TMEM; the epilogue
 //     adds 2^23 (so the integer sum sits in the mantissa), takes bit 0 of
 //     each of the 8 values of a coded byte and packs them.
 // Work item = (generation, 16 coded packets); the CTA loops over all column
-// tiles of the item.  Roles: 8 producer warps (A), 4 epilogue warps (D),
-// 1 warp that owns TMEM and issues the MMAs.  Every mbarrier wait is bounded
+// tiles of the item.  Roles, all running concurrently: 2 warps build B for
+// the next item into the other of two B buffers (a two-entry item ring in
+// shared memory hands the item index to the other roles); 16 producer warps
+// fill A (double-buffered in TMEM), prefetching the next tile's source bytes;
+// 1 thread issues the MMAs; 8 epilogue warps drain D (double-buffered).  Every mbarrier wait is bounded
 // by the global timer; a wait that gives up records GF_ETIMEOUT in the
 // library's device status word, the CTA drains its MMAs (bounded), frees
 // TMEM and exits.
@@ -39,30 +42,37 @@ namespace gf {
 
 namespace tc {
 
-constexpr int kProducerWarps = 8;
-constexpr int kEpilogueWarps = 4;
-constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1) * 32;  // 416
-constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;               // warp 12
+constexpr int kProducerWarps = 16;  // 4 per TMEM lane quarter, 16 sources each
+constexpr int kEpilogueWarps = 8;   // 4 per D half (one per lane quarter)
+constexpr int kBWarps = 4;          // coefficient bit matrices (B)
+constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;  // warp 24
+constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
+constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
-constexpr int kCodedPerItem = 16;   // coded packets per item (MMA N = 128 output bits)
-constexpr int kMaxSrc = 128;        // N limit of this path (B resident: 8N x 128 bytes)
-constexpr int kChunkSrc = 64;       // sources per A fill (128 TMEM columns)
+constexpr int kCodedPerHalf = 16;   // coded packets per D half (MMA N = 128 output bits)
+constexpr int kCodedPerItem = 32;   // coded packets per work item (two D halves)
+constexpr int kMaxSrc = 64;         // N limit of this path (A: 128 TMEM columns, B: 128 KB)
+constexpr int kSrcPerProducer = 16;
 constexpr int kTmemCols = 512;
-constexpr int kABufCols = 128;
-constexpr int kDCol0 = 256;         // D buffers at columns 256 and 384
+constexpr int kABufCols = 128;      // A buffers at columns 0 and 128
+constexpr int kDCol0 = 256;         // D halves at columns 256 and 384
 constexpr uint32_t kOne = 0x38u;    // 1.0 in E4M3
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
+constexpr uint32_t kSuspendNs = 100000;                 // try_wait suspend hint
+constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
-constexpr int kBBytes = kMaxSrc * 8 * 128;  // 128 KB: B, 8 K-blocks of 16 KB
+constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes
+constexpr int kBBytes = 4 * kKBlock;        // 128 KB: B of one item (K <= 512)
 constexpr int kTabBytes = 256 * 8 * 8;      // 16 KB: 8x8 FP8 block of every coefficient
-constexpr int kSmemBytes = kBBytes + kTabBytes + 1024 /*barriers etc*/ + 1024 /*alignment slack*/;
+constexpr int kSmemBytes = kBBytes + kTabBytes + 1024 /*control*/ + 1024 /*alignment slack*/;
 
 struct Ctl {
-    unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2], drain;
+    unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
+    unsigned long long info_full[2], info_empty[2], b_full, b_empty, drain;
+    long long ring_item[2];
     uint32_t tmem_base;
     int abort;
-    long long item;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -89,10 +99,10 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, uint32_t parit
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -117,6 +127,7 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, uint32_t
     int ok = 0;
     if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();  // lane 0's acquire of the barrier phase covers the whole warp
     return ok != 0;
 }
 
@@ -151,13 +162,15 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr)
         : "memory");
 }
@@ -178,18 +191,17 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(128 >> 3) << 17) |
                             ((uint32_t)(128 >> 4) << 24);
 
-// byte offset of (row n, K byte k) inside B (K-major, 128B swizzle, K-blocks of 128 bytes)
-__device__ __forceinline__ uint32_t b_offset(int n, int k)
+// byte offset of 16-byte chunk m of K-block kb in row n (K-major, 128B swizzle)
+__device__ __forceinline__ uint32_t b_chunk_offset(int n, int kb, int m)
 {
-    const int kb = k >> 7, kk = k & 127;
-    return (uint32_t)(kb * (128 * 128) + (n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 4) ^ (n & 7)) << 4) | (kk & 15)));
+    return (uint32_t)(kb * (128 * 128) + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
 }
 
 // 8 FP8 values (bytes j = 0..7) of one source byte: 1.0 where bit j is set
 __device__ __forceinline__ void spread_bits(uint32_t b, uint32_t &lo, uint32_t &hi)
 {
     lo = (((b & 0xFu) * 0x00204081u) & 0x01010101u) * kOne;
-    hi = ((((b >> 4) & 0xFu) * 0x00204081u) & 0x01010101u) * kOne;
+    hi = (((b >> 4) * 0x00204081u) & 0x01010101u) * kOne;
 }
 
 // parity byte of 8 FP32 sums (columns 8k'..8k'+7 = output bits r = 0..7)
@@ -203,6 +215,40 @@ __device__ __forceinline__ uint32_t parity_byte(const uint32_t *v)
     return ((q0 * 0x01020408u) >> 24) | (((q1 * 0x01020408u) >> 24) << 4);
 }
 
+__device__ __forceinline__ int locate(const long long *tile_start, int n_gens, long long item)
+{
+    int lo = 0, hi = n_gens - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// this producer thread's 16 source bytes of column `col` (0 outside the generation)
+__device__ __forceinline__ void load_sources(const EncGen &g, int ibase, unsigned long long col,
+                                             uint32_t (&b)[kSrcPerProducer])
+{
+    const unsigned long long len = g.len;
+    const uint8_t *p = g.src + (size_t)ibase * len + col;
+    if (col < len && ibase + kSrcPerProducer <= g.n_src) {
+#pragma unroll
+        for (int t = 0; t < kSrcPerProducer; ++t) b[t] = (uint32_t)__ldg(p + (size_t)t * len);
+    } else {
+#pragma unroll
+        for (int t = 0; t < kSrcPerProducer; ++t)
+            b[t] = (col < len && ibase + t < g.n_src) ? (uint32_t)__ldg(p + (size_t)t * len) : 0u;
+    }
+}
+
+// Shared-memory offset of 16-byte chunk m of K-block kb in B row n (K-major,
+// 128-byte swizzle: 8-row atoms of 1024 bytes, chunk index XOR row % 8).
+__device__ __forceinline__ uint32_t b_chunk(int n, int kb, int m)
+{
+    return (uint32_t)(kb * kKBlock + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__restrict__ tile_start, int n_gens,
                         long long total, WorkCounter *ctr, int *status)
@@ -213,6 +259,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [c][r]
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes);
     volatile int *abort_flag = &ctl->abort;
+    volatile long long *ring = ctl->ring_item;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -232,8 +279,12 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             mbar_init(&ctl->a_full[b], kProducerWarps * 32);
             mbar_init(&ctl->a_empty[b], 1);
             mbar_init(&ctl->d_full[b], 1);
-            mbar_init(&ctl->d_empty[b], kEpilogueWarps * 32);
+            mbar_init(&ctl->d_empty[b], (kEpilogueWarps / 2) * 32);
+            mbar_init(&ctl->info_full[b], 1);
+            mbar_init(&ctl->info_empty[b], kProducerWarps + kEpilogueWarps + 1);
         }
+        mbar_init(&ctl->b_full, kBWarps * 32);
+        mbar_init(&ctl->b_empty, 1);
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -250,80 +301,109 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    // per-role pipeline counters (every role walks the same sequence)
-    uint32_t fills = 0, tiles = 0;
-
-    for (;;) {
-        if (tid == 0) ctl->item = (long long)atomicAdd(&ctr->next, 1ull);
-        __syncthreads();
-        const long long item = ctl->item;
-        if (item >= total || *abort_flag) break;
-        // locate the generation
-        int lo = 0, hi = n_gens - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(tile_start + mid) <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        const EncGen g = gens[lo];
-        const int kc = (int)(item - __ldg(tile_start + lo));
-        const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
-        const unsigned long long len = g.len;
-        const int k0 = kc * kCodedPerItem;
-        const int nchunks = (N + kChunkSrc - 1) / kChunkSrc;
-        const int ncols = (int)((len + kColTile - 1) / kColTile);
-        const int kbytes = ((N + 15) / 16) * 128;  // B K extent, whole K-blocks
-
-        // B: rows n = 8k'+r, K bytes 8i+j; zero outside the generation
-        for (int e = tid; e < 128 * (kbytes / 16); e += blockDim.x) {
-            const int n = e / (kbytes / 16);
-            const int chunk = e - n * (kbytes / 16);  // 16-byte chunk = sources 2*chunk, 2*chunk+1
-            const int kp = n >> 3, r = n & 7, k = k0 + kp;
-            const int i0 = 2 * chunk, i1 = i0 + 1;
-            unsigned long long v0 = 0, v1 = 0;
-            if (k < K) {
-                if (i0 < N) v0 = tab[__ldg(g.coef + (size_t)k * ld + i0) * 8 + r];
-                if (i1 < N) v1 = tab[__ldg(g.coef + (size_t)k * ld + i1) * 8 + r];
+    if (warp >= kBWarp0) {
+        // ------------- B builder: publishes the next item, then its bit matrices -------------
+        const int bt = tid - kBWarp0 * 32;
+        const int m = bt & 7;            // 16-byte chunk in a K-block: sources 2m, 2m+1
+        const int kb = (bt >> 3) & 3;    // K-block: sources 16kb .. 16kb+15
+        const int kq = bt >> 5;          // coded packets 8kq .. 8kq+7 of the item
+        for (uint32_t seq = 0;; ++seq) {
+            const uint32_t e = seq & 1u, use = seq >> 1;
+            if (bt == 0) {
+                const bool ok = mbar_wait(&ctl->info_empty[e], (use & 1u) ^ 1u, abort_flag);
+                long long it = ok ? (long long)atomicAdd(&ctr->next, 1ull) : kSentinel;
+                if (it >= total) it = kSentinel;
+                if (!ok) ctl->abort = 1;
+                ring[e] = it;
+                mbar_arrive(&ctl->info_full[e]);
             }
-            uint4 q;
-            q.x = (uint32_t)v0;
-            q.y = (uint32_t)(v0 >> 32);
-            q.z = (uint32_t)v1;
-            q.w = (uint32_t)(v1 >> 32);
-            *reinterpret_cast<uint4 *>(Bs + b_offset(n, 16 * chunk)) = q;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-
-        if (warp < kProducerWarps) {
-            // ---------------- producers: A = source bit planes -> TMEM ----------------
-            const int half = warp >> 2;      // which 32 sources of a 64-source chunk
-            const int lrow = (warp & 3) * 32;  // TMEM lane quarter
-            const int pos = lrow + lane;       // byte position within the column tile
-            for (int ct = 0; ct < ncols && !*abort_flag; ++ct) {
-                const unsigned long long col = (unsigned long long)ct * kColTile + pos;
-                const bool in = col < len;
-                for (int ch = 0; ch < nchunks; ++ch) {
-                    const uint32_t buf = fills & 1u, use = fills >> 1;
-                    // gather this thread's 32 source bytes first (loads in flight together)
-                    uint32_t bytes[32];
-                    const int ibase = ch * kChunkSrc + half * 32;
+            asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
+            const long long item = ring[e];
+            if (item == kSentinel) break;
+            const int gi = locate(tile_start, n_gens, item);
+            const EncGen g = gens[gi];
+            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + kq * 8;
+            const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
+            const int nkb = (N + 15) / 16;
+            const int i0 = 16 * kb + 2 * m, i1 = i0 + 1;
+            uint32_t c0[8], c1[8];
 #pragma unroll
-                    for (int t = 0; t < 32; ++t) {
-                        const int i = ibase + t;
-                        bytes[t] = (in && i < N) ? (uint32_t)__ldg(g.src + (size_t)i * len + col) : 0u;
+            for (int t = 0; t < 8; ++t) {
+                const int k = k0 + t;
+                c0[t] = (kb < nkb && k < K && i0 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i0) : 0u;
+                c1[t] = (kb < nkb && k < K && i1 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i1) : 0u;
+            }
+            // B is single-buffered: wait until the MMAs of the previous item are done
+            bool ok = true;
+            if (bt == 0) ok = mbar_wait(&ctl->b_empty, (seq & 1u) ^ 1u, abort_flag);
+            if (bt == 0 && !ok) ctl->abort = 1;
+            asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
+            if (kb < nkb) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int kp = kq * 8 + t;
+                    const bool live = k0 + t < K;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const unsigned long long v0 = live ? tab[c0[t] * 8 + r] : 0ull;
+                        const unsigned long long v1 = live ? tab[c1[t] * 8 + r] : 0ull;
+                        uint4 q;
+                        q.x = (uint32_t)v0;
+                        q.y = (uint32_t)(v0 >> 32);
+                        q.z = (uint32_t)v1;
+                        q.w = (uint32_t)(v1 >> 32);
+                        *reinterpret_cast<uint4 *>(Bs + b_chunk(8 * kp + r, kb, m)) = q;
                     }
-                    if (!mbar_wait_warp(&ctl->a_empty[buf], (use & 1u) ^ 1u, abort_flag)) {
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&ctl->b_full);
+            if (*abort_flag) break;
+        }
+    } else if (warp < kProducerWarps) {
+        // ---------------- producers: A = source bit planes -> TMEM ----------------
+        const int quarter = warp & 3;          // TMEM lane quarter
+        const int part = warp >> 2;            // which 16 sources of the 64
+        const int pos = quarter * 32 + lane;   // byte position within the column tile
+        uint32_t fills = 0;
+        for (uint32_t seq = 0;; ++seq) {
+            const uint32_t e = seq & 1u, use = seq >> 1;
+            if (!mbar_wait_warp(&ctl->info_full[e], use & 1u, abort_flag)) {
+                ctl->abort = 1;
+                break;
+            }
+            const long long item = ring[e];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
+            if (item < 0) break;
+            const int gi = locate(tile_start, n_gens, item);
+            const EncGen g = gens[gi];
+            const int ncols = (int)((g.len + kColTile - 1) / kColTile);
+            const int ibase = part * kSrcPerProducer;
+            uint32_t bx[kSrcPerProducer], by[kSrcPerProducer];
+            load_sources(g, ibase, (unsigned long long)pos, bx);
+            bool ok = true;
+            for (int ct = 0; ct < ncols && ok; ct += 2) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = ct + h;
+                    if (c >= ncols) break;
+                    uint32_t(&cur)[kSrcPerProducer] = h == 0 ? bx : by;
+                    uint32_t(&nxt)[kSrcPerProducer] = h == 0 ? by : bx;
+                    if (c + 1 < ncols) load_sources(g, ibase, (unsigned long long)(c + 1) * kColTile + pos, nxt);
+                    const uint32_t buf = fills & 1u, fu = fills >> 1;
+                    if (!mbar_wait_warp(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag)) {
                         ctl->abort = 1;
+                        ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t acol = tmem + ((uint32_t)lrow << 16) + buf * kABufCols + half * 64;
+                    const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 32;
 #pragma unroll
-                    for (int grp = 0; grp < 4; ++grp) {
+                    for (int grp = 0; grp < 2; ++grp) {
                         uint32_t v[16];
 #pragma unroll
-                        for (int t = 0; t < 8; ++t) spread_bits(bytes[grp * 8 + t], v[2 * t], v[2 * t + 1]);
+                        for (int t = 0; t < 8; ++t) spread_bits(cur[grp * 8 + t], v[2 * t], v[2 * t + 1]);
                         tmem_st16(acol + grp * 16, v);
                     }
                     tmem_wait_st();
@@ -332,76 +412,131 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     ++fills;
                 }
             }
-        } else if (warp < kProducerWarps + kEpilogueWarps) {
-            // ---------------- epilogue: D -> parity bytes -> global ----------------
-            const int q = warp - kProducerWarps;  // TMEM lane quarter (warp % 4)
-            const int pos = q * 32 + lane;
-            for (int ct = 0; ct < ncols && !*abort_flag; ++ct) {
-                const uint32_t buf = tiles & 1u, use = tiles >> 1;
-                if (!mbar_wait_warp(&ctl->d_full[buf], use & 1u, abort_flag)) {
+            if (!ok) break;
+        }
+    } else if (warp < kProducerWarps + kEpilogueWarps) {
+        // ---------------- epilogue: D half -> parity bytes -> global ----------------
+        const int quarter = warp & 3;
+        const int half = (warp - kProducerWarps) >> 2;  // D half = coded packets 16*half .. +15
+        const int pos = quarter * 32 + lane;
+        uint32_t tiles = 0;
+        for (uint32_t seq = 0;; ++seq) {
+            const uint32_t e = seq & 1u, use = seq >> 1;
+            if (!mbar_wait_warp(&ctl->info_full[e], use & 1u, abort_flag)) {
+                ctl->abort = 1;
+                break;
+            }
+            const long long item = ring[e];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
+            if (item < 0) break;
+            const int gi = locate(tile_start, n_gens, item);
+            const EncGen g = gens[gi];
+            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + half * kCodedPerHalf;
+            const int K = g.n_coded;
+            const unsigned long long len = g.len;
+            const int ncols = (int)((len + kColTile - 1) / kColTile);
+            bool ok = true;
+            for (int ct = 0; ct < ncols; ++ct) {
+                if (!mbar_wait_warp(&ctl->d_full[half], tiles & 1u, abort_flag)) {
                     ctl->abort = 1;
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + half * 128;
                 const unsigned long long col = (unsigned long long)ct * kColTile + pos;
-                const uint32_t dcol = tmem + ((uint32_t)(q * 32) << 16) + kDCol0 + buf * 128;
-                uint32_t outb[16];
+                uint8_t *o = g.out + (size_t)k0 * len + col;
 #pragma unroll
-                for (int grp = 0; grp < 8; ++grp) {
-                    uint32_t v[16];
-                    tmem_ld16(dcol + grp * 16, v);
-                    tmem_wait_ld();
-                    outb[2 * grp] = parity_byte(v);
-                    outb[2 * grp + 1] = parity_byte(v + 8);
-                }
-                tc_fence_before();
-                mbar_arrive(&ctl->d_empty[buf]);
-                if (col < len) {
+                for (int pr = 0; pr < 2; ++pr) {
+                    uint32_t outb[8];
 #pragma unroll
-                    for (int kp = 0; kp < kCodedPerItem; ++kp)
-                        if (k0 + kp < K) g.out[(size_t)(k0 + kp) * len + col] = (uint8_t)outb[kp];
+                    for (int g2 = 0; g2 < 2; ++g2) {
+                        uint32_t v[32];
+                        tmem_ld32(dcol + (pr * 2 + g2) * 32, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) outb[g2 * 4 + t] = parity_byte(v + 8 * t);
+                    }
+                    if (pr == 1) {
+                        tc_fence_before();
+                        mbar_arrive(&ctl->d_empty[half]);
+                    }
+                    if (col < len) {
+#pragma unroll
+                        for (int kp = 0; kp < 8; ++kp)
+                            if (k0 + pr * 8 + kp < K) o[(size_t)(pr * 8 + kp) * len] = (uint8_t)outb[kp];
+                    }
                 }
                 ++tiles;
             }
-        } else if (lane == 0) {
-            // ---------------- MMA issuer ----------------
+            if (!ok) break;
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer (warp kMmaWarp, one thread) ----------------
+        uint32_t fills = 0, tiles = 0;
+        for (uint32_t seq = 0;; ++seq) {
+            const uint32_t e = seq & 1u, use = seq >> 1;
+            if (!mbar_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
+                ctl->abort = 1;
+                break;
+            }
+            const long long item = ring[e];
+            mbar_arrive(&ctl->info_empty[e]);
+            if (item < 0) break;
+            const int gi = locate(tile_start, n_gens, item);
+            const EncGen g = gens[gi];
+            const int ncols = (int)((g.len + kColTile - 1) / kColTile);
+            const int ksteps = (g.n_src + 3) / 4;  // 4 sources = 32 FP8 per MMA
+            const int k_item = g.n_coded - (int)(item - __ldg(tile_start + gi)) * kCodedPerItem;
+            const int halves = k_item > kCodedPerHalf ? 2 : 1;
+            bool ok = mbar_wait(&ctl->b_full, seq & 1u, abort_flag);
+            tc_fence_after();
             const uint32_t b_base = smem_u32(Bs);
-            for (int ct = 0; ct < ncols && !*abort_flag; ++ct) {
-                const uint32_t dbuf = tiles & 1u, duse = tiles >> 1;
-                if (!mbar_wait(&ctl->d_empty[dbuf], (duse & 1u) ^ 1u, abort_flag)) {
-                    ctl->abort = 1;
+            for (int ct = 0; ct < ncols && ok; ++ct) {
+                const uint32_t buf = fills & 1u, fu = fills >> 1;
+                if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
+                    ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem + kDCol0 + dbuf * 128;
-                bool ok = true;
-                for (int ch = 0; ch < nchunks; ++ch) {
-                    const uint32_t buf = fills & 1u, use = fills >> 1;
-                    if (!mbar_wait(&ctl->a_full[buf], use & 1u, abort_flag)) {
-                        ctl->abort = 1;
+                for (int h = 0; h < halves; ++h) {
+                    if (!mbar_wait(&ctl->d_empty[h], (tiles & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const int nsrc = min(kChunkSrc, N - ch * kChunkSrc);
-                    const int ksteps = (nsrc + 3) / 4;  // 4 sources = 32 FP8 per MMA
+                    const uint32_t dt = tmem + kDCol0 + h * 128;
                     for (int s = 0; s < ksteps; ++s) {
-                        const int kglob = ch * kChunkSrc * 8 + s * 32;  // byte offset in K
-                        const uint32_t baddr = b_base + (uint32_t)((kglob >> 7) * (128 * 128) + (kglob & 127));
-                        tc_mma(dt, tmem + buf * kABufCols + s * 8, b_desc(baddr), kIdesc,
-                               (ch > 0 || s > 0) ? 1u : 0u);
+                        const int kglob = s * 32;  // byte offset in K
+                        const uint32_t baddr =
+                            b_base + (uint32_t)((kglob >> 7) * kKBlock + h * (128 * 128) + (kglob & 127));
+                        tc_mma(dt, tmem + buf * kABufCols + s * 8, b_desc(baddr), kIdesc, s > 0 ? 1u : 0u);
                     }
-                    tc_commit(&ctl->a_empty[buf]);
-                    ++fills;
+                    tc_commit(&ctl->d_full[h]);
                 }
                 if (!ok) break;
-                tc_commit(&ctl->d_full[dbuf]);
+                if (halves == 1) {
+                    // keep both halves' phases in step: the idle half completes an empty phase
+                    if (!mbar_wait(&ctl->d_empty[1], (tiles & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_commit(&ctl->d_full[1]);
+                }
+                tc_commit(&ctl->a_empty[buf]);
+                ++fills;
                 ++tiles;
             }
+            tc_commit(&ctl->b_empty);
+            if (!ok) {
+                ctl->abort = 1;
+                break;
+            }
         }
-        __syncthreads();  // item done: D drained, B may be rewritten
     }
 
+    __syncthreads();
     // drain: wait (bounded) for every MMA this CTA issued, then free TMEM
     if (warp == kMmaWarp) {
         if (lane == 0) {
