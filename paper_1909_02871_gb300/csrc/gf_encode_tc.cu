@@ -22,11 +22,13 @@
 //     adds 2^23 (so the integer sum sits in the mantissa), takes bit 0 of
 //     each of the 8 values of a coded byte and packs them.
 // Work item = (generation, 16 coded packets); the CTA loops over all column
-// tiles of the item.  Roles, all running concurrently: 2 warps build B for
-// the next item into the other of two B buffers (a two-entry item ring in
-// shared memory hands the item index to the other roles); 16 producer warps
-// fill A (double-buffered in TMEM), prefetching the next tile's source bytes;
-// 1 thread issues the MMAs; 8 epilogue warps drain D (double-buffered).  Every mbarrier wait is bounded
+// tiles of the item, one 128-byte column tile at a time, and each A fill
+// (128 positions x up to 64 sources) serves 32 coded packets: two MMA
+// streams of N = 128 into two D halves.  Roles, all running concurrently:
+// 2 warps publish the next item in a two-entry ring and build its B; 8
+// producer warps stage their source rows in shared memory with cp.async two
+// tiles ahead and fill A (double-buffered in TMEM); 1 thread issues the
+// MMAs; 16 epilogue warps drain the D halves.  Every mbarrier wait is bounded
 // by the global timer; a wait that gives up records GF_ETIMEOUT in the
 // library's device status word, the CTA drains its MMAs (bounded), frees
 // TMEM and exits.
@@ -42,17 +44,19 @@ namespace gf {
 
 namespace tc {
 
-constexpr int kProducerWarps = 16;  // 4 per TMEM lane quarter, 16 sources each
-constexpr int kEpilogueWarps = 8;   // 4 per D half (one per lane quarter)
-constexpr int kBWarps = 4;          // coefficient bit matrices (B)
+constexpr int kProducerWarps = 8;   // 2 per TMEM lane quarter, 32 sources each
+constexpr int kEpilogueWarps = 16;  // 4 per lane quarter, 8 coded packets each
+constexpr int kBWarps = 2;          // coefficient bit matrices (B)
 constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;  // warp 24
-constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
-constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
+constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25, 26
+constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 864
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerHalf = 16;   // coded packets per D half (MMA N = 128 output bits)
 constexpr int kCodedPerItem = 32;   // coded packets per work item (two D halves)
 constexpr int kMaxSrc = 64;         // N limit of this path (A: 128 TMEM columns, B: 128 KB)
-constexpr int kSrcPerProducer = 16;
+constexpr int kSrcPerProducer = 32;
+constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
+constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte positions
 constexpr int kTmemCols = 512;
 constexpr int kABufCols = 128;      // A buffers at columns 0 and 128
 constexpr int kDCol0 = 256;         // D halves at columns 256 and 384
@@ -65,7 +69,8 @@ constexpr long long kSentinel = -1;
 constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes
 constexpr int kBBytes = 4 * kKBlock;        // 128 KB: B of one item (K <= 512)
 constexpr int kTabBytes = 256 * 8 * 8;      // 16 KB: 8x8 FP8 block of every coefficient
-constexpr int kSmemBytes = kBBytes + kTabBytes + 1024 /*control*/ + 1024 /*alignment slack*/;
+constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
+constexpr int kSmemBytes = kBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*alignment slack*/;
 
 struct Ctl {
     unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
@@ -226,20 +231,44 @@ __device__ __forceinline__ int locate(const long long *tile_start, int n_gens, l
     return lo;
 }
 
-// this producer thread's 16 source bytes of column `col` (0 outside the generation)
-__device__ __forceinline__ void load_sources(const EncGen &g, int ibase, unsigned long long col,
-                                             uint32_t (&b)[kSrcPerProducer])
+// this producer thread's 32 source bytes of column `col` straight from
+// global memory (generations whose rows are not 4-byte aligned)
+__device__ __forceinline__ void load_direct(const EncGen &g, int ibase, unsigned long long col, uint32_t (&b)[8],
+                                            int grp)
 {
     const unsigned long long len = g.len;
-    const uint8_t *p = g.src + (size_t)ibase * len + col;
-    if (col < len && ibase + kSrcPerProducer <= g.n_src) {
 #pragma unroll
-        for (int t = 0; t < kSrcPerProducer; ++t) b[t] = (uint32_t)__ldg(p + (size_t)t * len);
-    } else {
-#pragma unroll
-        for (int t = 0; t < kSrcPerProducer; ++t)
-            b[t] = (col < len && ibase + t < g.n_src) ? (uint32_t)__ldg(p + (size_t)t * len) : 0u;
+    for (int t = 0; t < 8; ++t) {
+        const int i = ibase + grp * 8 + t;
+        b[t] = (col < len && i < g.n_src) ? (uint32_t)__ldg(g.src + (size_t)i * len + col) : 0u;
     }
+}
+
+// Stage this warp's 32 sources x 32 byte positions of column tile `ct` into
+// shared memory with 4-byte cp.async (rows 4-byte aligned); bytes outside
+// the generation are zero-filled.
+__device__ __forceinline__ void stage_tile(const EncGen &g, int ibase, int quarter, int ct, unsigned char *stage,
+                                           int lane)
+{
+    const unsigned long long len = g.len;
+    const unsigned long long c0 = (unsigned long long)ct * kColTile + quarter * 32;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int w = lane + 32 * j;      // word of the 32 x 32-byte block
+        const int row = w >> 3, wc = w & 7;
+        const int i = ibase + row;
+        const unsigned long long col = c0 + 4 * wc;
+        uint32_t bytes = 0;
+        const uint8_t *src = g.src;
+        if (i < g.n_src && col < len) {
+            bytes = (uint32_t)min(4ull, len - col);
+            src = g.src + (size_t)i * len + col;
+        }
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(stage + row * 32 + 4 * wc)),
+                     "l"(src), "r"(bytes)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Shared-memory offset of 16-byte chunk m of K-block kb in B row n (K-major,
@@ -257,7 +286,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Bs = smem;
     unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [c][r]
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes);
+    unsigned char *staging = smem + kBBytes + kTabBytes;
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes + kStageAll);
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
@@ -276,14 +306,14 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&ctl->a_full[b], kProducerWarps * 32);
+            mbar_init(&ctl->a_full[b], kProducerWarps);
             mbar_init(&ctl->a_empty[b], 1);
             mbar_init(&ctl->d_full[b], 1);
-            mbar_init(&ctl->d_empty[b], (kEpilogueWarps / 2) * 32);
+            mbar_init(&ctl->d_empty[b], kEpilogueWarps / 2);
             mbar_init(&ctl->info_full[b], 1);
             mbar_init(&ctl->info_empty[b], kProducerWarps + kEpilogueWarps + 1);
         }
-        mbar_init(&ctl->b_full, kBWarps * 32);
+        mbar_init(&ctl->b_full, 1);
         mbar_init(&ctl->b_empty, 1);
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
@@ -306,7 +336,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int bt = tid - kBWarp0 * 32;
         const int m = bt & 7;            // 16-byte chunk in a K-block: sources 2m, 2m+1
         const int kb = (bt >> 3) & 3;    // K-block: sources 16kb .. 16kb+15
-        const int kq = bt >> 5;          // coded packets 8kq .. 8kq+7 of the item
+        const int kq0 = bt >> 5;         // coded-packet octets kq0, kq0 + 2
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (bt == 0) {
@@ -322,16 +352,17 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item == kSentinel) break;
             const int gi = locate(tile_start, n_gens, item);
             const EncGen g = gens[gi];
-            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + kq * 8;
+            const int kbase = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem;
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
             const int nkb = (N + 15) / 16;
             const int i0 = 16 * kb + 2 * m, i1 = i0 + 1;
-            uint32_t c0[8], c1[8];
+            uint32_t cc[16];  // coefficient pair (c[k][i0], c[k][i1]) packed in 16 bits
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int k = k0 + t;
-                c0[t] = (kb < nkb && k < K && i0 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i0) : 0u;
-                c1[t] = (kb < nkb && k < K && i1 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i1) : 0u;
+            for (int t = 0; t < 16; ++t) {
+                const int k = kbase + (kq0 + 2 * (t >> 3)) * 8 + (t & 7);
+                const uint32_t a = (kb < nkb && k < K && i0 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i0) : 0u;
+                const uint32_t b = (kb < nkb && k < K && i1 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i1) : 0u;
+                cc[t] = a | (b << 8);
             }
             // B is single-buffered: wait until the MMAs of the previous item are done
             bool ok = true;
@@ -340,13 +371,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
             if (kb < nkb) {
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int kp = kq * 8 + t;
-                    const bool live = k0 + t < K;
+                for (int t = 0; t < 16; ++t) {
+                    const int kp = (kq0 + 2 * (t >> 3)) * 8 + (t & 7);
+                    const bool live = kbase + kp < K;
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
-                        const unsigned long long v0 = live ? tab[c0[t] * 8 + r] : 0ull;
-                        const unsigned long long v1 = live ? tab[c1[t] * 8 + r] : 0ull;
+                        const unsigned long long v0 = live ? tab[(cc[t] & 0xFFu) * 8 + r] : 0ull;
+                        const unsigned long long v1 = live ? tab[(cc[t] >> 8) * 8 + r] : 0ull;
                         uint4 q;
                         q.x = (uint32_t)v0;
                         q.y = (uint32_t)(v0 >> 32);
@@ -357,14 +388,17 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&ctl->b_full);
+            asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
+            if (bt == 0) mbar_arrive(&ctl->b_full);
             if (*abort_flag) break;
         }
     } else if (warp < kProducerWarps) {
         // ---------------- producers: A = source bit planes -> TMEM ----------------
         const int quarter = warp & 3;          // TMEM lane quarter
-        const int part = warp >> 2;            // which 16 sources of the 64
+        const int part = warp >> 2;            // which 32 sources of the 64
         const int pos = quarter * 32 + lane;   // byte position within the column tile
+        const int ibase = part * kSrcPerProducer;
+        unsigned char *stage = staging + warp * (kStages * kStageBytes);
         uint32_t fills = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
@@ -379,45 +413,64 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int gi = locate(tile_start, n_gens, item);
             const EncGen g = gens[gi];
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
-            const int ibase = part * kSrcPerProducer;
-            uint32_t bx[kSrcPerProducer], by[kSrcPerProducer];
-            load_sources(g, ibase, (unsigned long long)pos, bx);
-            bool ok = true;
-            for (int ct = 0; ct < ncols && ok; ct += 2) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = ct + h;
-                    if (c >= ncols) break;
-                    uint32_t(&cur)[kSrcPerProducer] = h == 0 ? bx : by;
-                    uint32_t(&nxt)[kSrcPerProducer] = h == 0 ? by : bx;
-                    if (c + 1 < ncols) load_sources(g, ibase, (unsigned long long)(c + 1) * kColTile + pos, nxt);
-                    const uint32_t buf = fills & 1u, fu = fills >> 1;
-                    if (!mbar_wait_warp(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag)) {
-                        ctl->abort = 1;
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 32;
-#pragma unroll
-                    for (int grp = 0; grp < 2; ++grp) {
-                        uint32_t v[16];
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) spread_bits(cur[grp * 8 + t], v[2 * t], v[2 * t + 1]);
-                        tmem_st16(acol + grp * 16, v);
-                    }
-                    tmem_wait_st();
-                    tc_fence_before();
-                    mbar_arrive(&ctl->a_full[buf]);
-                    ++fills;
+            const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
+            if (staged) {
+                // always kStages-1 groups in flight before the loop (empty ones past the row end)
+                for (int p = 0; p < kStages - 1; ++p) {
+                    if (p < ncols) stage_tile(g, ibase, quarter, p, stage + p * kStageBytes, lane);
+                    else asm volatile("cp.async.commit_group;" ::: "memory");
                 }
             }
+            bool ok = true;
+            for (int ct = 0; ct < ncols; ++ct) {
+                if (staged) {
+                    __syncwarp();  // every lane is done reading the stage about to be refilled
+                    if (ct + kStages - 1 < ncols)
+                        stage_tile(g, ibase, quarter, ct + kStages - 1, stage + ((ct + kStages - 1) % kStages) * kStageBytes,
+                                   lane);
+                    else
+                        asm volatile("cp.async.commit_group;" ::: "memory");
+                    asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+                    __syncwarp();
+                }
+                const uint32_t buf = fills & 1u, fu = fills >> 1;
+                if (!mbar_wait_warp(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag)) {
+                    ctl->abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 64;
+                const unsigned char *sb = stage + (ct % kStages) * kStageBytes + lane;
+#pragma unroll
+                for (int grp = 0; grp < 4; ++grp) {
+                    uint32_t b[8];
+                    if (staged) {
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) b[t] = sb[(grp * 8 + t) * 32];
+                    } else {
+                        load_direct(g, ibase, (unsigned long long)ct * kColTile + pos, b, grp);
+                    }
+                    uint32_t v[16];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) spread_bits(b[t], v[2 * t], v[2 * t + 1]);
+                    tmem_st16(acol + grp * 16, v);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->a_full[buf]);
+                ++fills;
+            }
+            if (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");
             if (!ok) break;
         }
     } else if (warp < kProducerWarps + kEpilogueWarps) {
-        // ---------------- epilogue: D half -> parity bytes -> global ----------------
+        // ---------------- epilogue: 64 D columns -> parity bytes -> global ----------------
         const int quarter = warp & 3;
-        const int half = (warp - kProducerWarps) >> 2;  // D half = coded packets 16*half .. +15
+        const int sub = (warp - kProducerWarps) >> 2;   // 0..3
+        const int half = sub >> 1;                       // D half
+        const int oct = sub & 1;                         // 8-packet group inside the half
         const int pos = quarter * 32 + lane;
         uint32_t tiles = 0;
         for (uint32_t seq = 0;; ++seq) {
@@ -432,7 +485,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item < 0) break;
             const int gi = locate(tile_start, n_gens, item);
             const EncGen g = gens[gi];
-            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + half * kCodedPerHalf;
+            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + half * kCodedPerHalf + oct * 8;
             const int K = g.n_coded;
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
@@ -444,29 +497,25 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + half * 128;
+                const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + half * 128 + oct * 64;
+                uint32_t outb[8];
+#pragma unroll
+                for (int g2 = 0; g2 < 2; ++g2) {
+                    uint32_t v[32];
+                    tmem_ld32(dcol + g2 * 32, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) outb[g2 * 4 + t] = parity_byte(v + 8 * t);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->d_empty[half]);
                 const unsigned long long col = (unsigned long long)ct * kColTile + pos;
-                uint8_t *o = g.out + (size_t)k0 * len + col;
+                if (col < len) {
+                    uint8_t *o = g.out + (size_t)k0 * len + col;
 #pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    uint32_t outb[8];
-#pragma unroll
-                    for (int g2 = 0; g2 < 2; ++g2) {
-                        uint32_t v[32];
-                        tmem_ld32(dcol + (pr * 2 + g2) * 32, v);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) outb[g2 * 4 + t] = parity_byte(v + 8 * t);
-                    }
-                    if (pr == 1) {
-                        tc_fence_before();
-                        mbar_arrive(&ctl->d_empty[half]);
-                    }
-                    if (col < len) {
-#pragma unroll
-                        for (int kp = 0; kp < 8; ++kp)
-                            if (k0 + pr * 8 + kp < K) o[(size_t)(pr * 8 + kp) * len] = (uint8_t)outb[kp];
-                    }
+                    for (int kp = 0; kp < 8; ++kp)
+                        if (k0 + kp < K) o[(size_t)kp * len] = (uint8_t)outb[kp];
                 }
                 ++tiles;
             }
@@ -492,7 +541,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int halves = k_item > kCodedPerHalf ? 2 : 1;
             bool ok = mbar_wait(&ctl->b_full, seq & 1u, abort_flag);
             tc_fence_after();
-            const uint32_t b_base = smem_u32(Bs);
+            const uint64_t bdesc0 = b_desc(smem_u32(Bs));
             for (int ct = 0; ct < ncols && ok; ++ct) {
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
                 if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
@@ -506,12 +555,17 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                         break;
                     }
                     tc_fence_after();
+                    // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
+                    // B lies below 256 KB of shared memory)
+                    const uint64_t dh = bdesc0 + (uint64_t)((h * (128 * 128)) >> 4);
                     const uint32_t dt = tmem + kDCol0 + h * 128;
-                    for (int s = 0; s < ksteps; ++s) {
-                        const int kglob = s * 32;  // byte offset in K
-                        const uint32_t baddr =
-                            b_base + (uint32_t)((kglob >> 7) * kKBlock + h * (128 * 128) + (kglob & 127));
-                        tc_mma(dt, tmem + buf * kABufCols + s * 8, b_desc(baddr), kIdesc, s > 0 ? 1u : 0u);
+                    const uint32_t at = tmem + buf * kABufCols;
+                    tc_mma(dt, at, dh, kIdesc, 0u);
+#pragma unroll
+                    for (int s = 1; s < 16; ++s) {
+                        if (s < ksteps)
+                            tc_mma(dt, at + s * 8, dh + (uint64_t)((((s * 32) >> 7) * kKBlock + ((s * 32) & 127)) >> 4),
+                                   kIdesc, 1u);
                     }
                     tc_commit(&ctl->d_full[h]);
                 }
