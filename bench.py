@@ -35,6 +35,24 @@ WORKLOAD = "uniform batched encode: 4096 generations x N=64 x 1500 B, K=64, GF(2
 N_GENS, N_SRC, N_CODED, LEN = 4096, 64, 64, 1500
 
 
+def _traffic(kernel_src: str, summary: str):
+    """DRAM bytes per launch recorded in profiles/ for a kernel, or None when
+    the kernel source no longer matches the hash the counters were taken on."""
+    import hashlib
+    try:
+        fields = {}
+        for line in open(os.path.join(ROOT, "profiles", summary)):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()
+        if sha.startswith(fields["source_sha256_prefix"]):
+            return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,7 +243,12 @@ def run_gf(args, rank, world, local_rank):
                 "kernel": "encode_table_kernel",
                 "peak_kind": "derived: 152 SMs x 128 int32 lanes x median SM clock"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = args.traffic
+    if args.traffic is not None:
+        roof["traffic"] = args.traffic
+    elif chosen[0] == gf.PATH_BITSLICED:
+        roof["traffic"] = _traffic("paper_1909_02871_gb300/csrc/gf_encode_tc.cu", "encode_bitsliced_traffic.txt")
+    else:
+        roof["traffic"] = None
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
