@@ -181,6 +181,34 @@ int gf_decode_batched(const gf_dec_t *gens, int n_gens, gf_stream_t stream);
  * reached rank < n_src, else GF_OK (GF_ECUDA on a CUDA error). */
 int gf_decode_check(const gf_dec_t *gens, int n_gens, gf_stream_t stream);
 
+/*
+ * gf_decode_noalloc: decode ONE generation exactly like gf_decode_batched, but
+ * without allocating anything: no cudaMalloc / cudaFree, no growth of the
+ * library workspace.  The paper has no counterpart; this entry point exists
+ * for callers that cannot let a decode call allocate device memory -- for
+ * example a packet data path that decodes each generation as its last packet
+ * arrives and must not wait on the allocator, or a process whose device
+ * memory is all owned by its own pool.
+ *
+ * Its scratch (the elimination transform, the descriptors and a work
+ * counter) is a fixed array of GF_NOALLOC_SCRATCH_BYTES in the library's
+ * device memory, present on every device that loads the library until the
+ * process exits.  Limits: n_src * n_recv <= GF_NOALLOC_SCRATCH_BYTES - 1024,
+ * and the n_src x (n_src + n_recv) elimination rows must fit one CTA's shared
+ * memory (e.g. n_src = 255 with n_recv <= 560 on GB300); larger inputs return
+ * GF_EINVAL.  Arguments as in gf_dec_t (device pointers; used and solved may
+ * be NULL), enqueued on `stream`.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current) and should be made before any stream capture.  Every call
+ * shares the one array, which keeps the last call's contents; calls whose
+ * work overlaps on the GPU (other streams or threads) race on it.
+ * Errors: GF_EINVAL, GF_ECUDA.
+ */
+#define GF_NOALLOC_SCRATCH_BYTES (256 * 1024)
+int gf_decode_noalloc(int field, int n_src, int n_recv, uint64_t len, const uint8_t *coef, const uint8_t *payload,
+                      uint8_t *out, int32_t *rank, int32_t *used, uint8_t *solved, gf_stream_t stream);
+
 /* ------------------------------------------------------------------ */
 /* Plans: pre-uploaded batches for CUDA graph capture                  */
 /* ------------------------------------------------------------------ */

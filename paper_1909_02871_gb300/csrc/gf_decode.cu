@@ -304,6 +304,19 @@ int launch_decode_coef(const DecodeWork &w, const DecGen *d_gens, cudaStream_t s
     return cuda_status(cudaGetLastError());
 }
 
+// Launch the coefficient phase on descriptors already in device memory.
+int launch_decode_coef_raw(const DecGen *d_gens, int n_gens, size_t smem, cudaStream_t stream)
+{
+    if (n_gens == 0) return GF_OK;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(decode_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return GF_ECUDA;
+    }
+    decode_coef_kernel<<<(unsigned)n_gens, kDecThreads, smem, stream>>>(d_gens);
+    return cuda_status(cudaGetLastError());
+}
+
 size_t decode_stage_bytes(const DecodeWork &w)
 {
     size_t b = align_up(w.gens.size() * sizeof(DecGen), 256);

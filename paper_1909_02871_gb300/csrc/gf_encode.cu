@@ -305,6 +305,21 @@ int launch_batch(const EncodeBatch &b, cudaStream_t stream)
     return cuda_status(cudaGetLastError());
 }
 
+// Tile count of one table-path generation (variant already chosen).
+long long table_tiles_for(EncGen &g) { return table_tiles(g); }
+
+// Launch the table-path kernel on descriptors already in device memory.
+int launch_table_raw(const EncGen *d_gens, const long long *d_tile_start, int n_gens, long long total,
+                     WorkCounter *ctr, cudaStream_t stream)
+{
+    if (total == 0) return GF_OK;
+    const long long warps = kEncThreads / 32;
+    long long grid = (total + warps - 1) / warps;
+    grid = std::min<long long>(grid, table_grid());
+    encode_table_kernel<<<(unsigned)grid, kEncThreads, 0, stream>>>(d_gens, d_tile_start, n_gens, total, ctr);
+    return cuda_status(cudaGetLastError());
+}
+
 int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBatch> &out)
 {
     out.clear();

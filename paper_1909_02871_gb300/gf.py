@@ -54,6 +54,9 @@ _SIGS = {
     "gf_encode_validate": (ctypes.c_int, [ctypes.POINTER(GfGen), ctypes.c_int, ctypes.c_void_p]),
     "gf_decode_batched": (ctypes.c_int, [ctypes.POINTER(GfDec), ctypes.c_int, ctypes.c_void_p]),
     "gf_decode_check": (ctypes.c_int, [ctypes.POINTER(GfDec), ctypes.c_int, ctypes.c_void_p]),
+    "gf_decode_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "gf_encode_plan_create": (ctypes.c_int, [ctypes.POINTER(GfGen), ctypes.c_int, ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_void_p)]),
     "gf_decode_plan_create": (ctypes.c_int, [ctypes.POINTER(GfDec), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -195,6 +198,14 @@ def decode_status(decs, stream=None) -> int:
 def gf_decode_check(decs, stream=None) -> int:
     arr, n = decs if isinstance(decs, tuple) else make_decs(decs)
     return load().gf_decode_check(arr, n, _stream(stream))
+
+
+def gf_decode_noalloc(field: int, n_src: int, n_recv: int, length: int, coef, payload, out, rank, used=None,
+                      solved=None, stream=None) -> int:
+    """Single-generation decode that allocates nothing (scratch in a fixed
+    device array of the library); returns the raw status."""
+    return int(load().gf_decode_noalloc(field, n_src, n_recv, length, _ptr(coef), _ptr(payload), _ptr(out),
+                                        _ptr(rank), _ptr(used), _ptr(solved), _stream(stream)))
 
 
 class Plan:
