@@ -356,12 +356,153 @@ def bench_e2e(gf, torch, dev, stream, src_h, coef_h, args, plan, src, coef, out)
             "ms_per_step": ms}
 
 
+# ---------------------------------------------------------------------------
+# other workloads (python bench.py --workload uneven|serve)
+# ---------------------------------------------------------------------------
+def run_uneven(args, rank, world, local_rank):
+    """Uneven batched encode + decode over a lossy channel: 2048 generations,
+    N ~ U{8..255}, len log-uniform in [64, 9000] B, field ~ U{GF(2), GF(4),
+    GF(16), GF(256)}, 10 % erasures; one step = one CUDA-graph replay of the
+    encode launch and the decode launches."""
+    import torch
+
+    from paper_1909_02871_gb300 import gf, pipeline, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    batch = synth.uneven_batch(n_gens=args.gens, index=0)
+    work = pipeline.build(batch, dev)
+    step = pipeline.UnevenStep(work)
+    stream = torch.cuda.Stream(device=dev)
+    step.capture(stream)
+    for _ in range(args.warmup):
+        step.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            for i in range(args.steps):
+                step.replay()
+                ev[i + 1].record(stream)
+        stream.synchronize()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    bad = [i for i in (0, 1, len(batch.gens) // 2, len(batch.gens) - 1)
+           if not np.array_equal(pipeline.decoded(work, i), batch.gens[i].src)]
+    # plain form on a subset, extrapolated by source bytes
+    sub = list(range(0, len(batch.gens), max(1, len(batch.gens) // 64)))
+    sub_bytes = sum(batch.gens[i].src.size for i in sub)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        pipeline.plain_step(work, sub, stream=stream)
+    stream.synchronize()
+    plain_s = time.perf_counter() - t0
+    value = work.bytes_src * args.steps / (total_ms / 1e3) / 1e9
+    line = {"metric": "uneven encode+decode GB/s (source bytes per step)", "value": value, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"uneven encode+decode: {len(batch.gens)} generations, N~U{{8..255}}, "
+                                   "len log-uniform 64-9000 B, field ~U{GF2,GF4,GF16,GF256}, 10% erasures",
+                       "source_bytes": work.bytes_src, "coded_bytes": work.bytes_coded,
+                       "packets_sent": int(sum(work.k_sent))},
+            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+            "gpu_launches": step.kernel_count * args.steps, "clocks": clk.summary(),
+            "round_trip_ok": not bad,
+            "plain": {"value": sub_bytes / plain_s / 1e9, "unit": "GB/s",
+                      "sample": f"{len(sub)} generations, one encode + one decode call each, host wall time"}}
+    step.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving: Poisson arrivals of encode and decode requests (shapes of the
+    uneven workload), admitted by device memory, decode packets arriving one
+    by one; throughput and p50/p99 latency at several arrival rates."""
+    import torch
+
+    from paper_1909_02871_gb300 import gf, serve, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    n = args.requests
+    batch = synth.uneven_batch(n_gens=n, index=7)
+    # coded packets of the decode requests, produced by the library (untimed)
+    coded = {}
+    items, keep = [], []
+    for i, ge in enumerate(batch.gens):
+        if i % 2 == 1:
+            c = np.ascontiguousarray(ge.coef_stream[~ge.erased])
+            s_d = torch.from_numpy(ge.src).to(dev)
+            c_d = torch.from_numpy(c).to(dev)
+            o_d = torch.empty((c.shape[0], ge.length), dtype=torch.uint8, device=dev)
+            keep.append((s_d, c_d, o_d))
+            items.append((ge.field, ge.n_src, c.shape[0], ge.length, s_d, c_d, o_d))
+            coded[i] = (c, o_d)
+    gf.gf_encode_batched(items)
+    torch.cuda.synchronize()
+    coded = {i: (c, o.cpu().numpy()) for i, (c, o) in coded.items()}
+    del keep
+
+    def requests(times, gap):
+        out = []
+        for i, (ge, t) in enumerate(zip(batch.gens, times)):
+            if i % 2 == 0:
+                out.append(serve.EncodeRequest(i, float(t), ge.field, ge.src,
+                                               np.ascontiguousarray(ge.coef_stream[:ge.n_src])))
+            else:
+                c, p = coded[i]
+                out.append(serve.DecodeRequest(i, float(t), ge.field, ge.n_src, ge.length, c, p,
+                                               float(t) + gap * np.arange(1, c.shape[0] + 1)))
+        return out
+
+    budget = 4 << 30
+    # saturation: everything arrives at once
+    reqs = requests(np.zeros(n), 0.0)
+    serve.Server(mem_budget=budget).run(reqs[:32])  # warm-up
+    reqs = requests(np.zeros(n), 0.0)
+    srv = serve.Server(mem_budget=budget)
+    wall = srv.run(reqs)
+    sat = n / wall
+    ok = all(np.array_equal(r.result, batch.gens[r.rid].src) for r in reqs if isinstance(r, serve.DecodeRequest))
+    plain_reqs = requests(np.zeros(n), 0.0)[:64]
+    plain_wall = serve.Server(mem_budget=budget, max_active=1).run(plain_reqs)
+    rates = {}
+    for f in (0.25, 0.5, 0.9):
+        rate = f * sat
+        r2 = requests(synth.arrivals(rate, n, index=int(f * 100)), 20e-6)
+        s2 = serve.Server(mem_budget=budget)
+        w2 = s2.run(r2)
+        st = serve.latency_stats(r2)
+        st.update({"rate_req_per_s": rate, "throughput_req_per_s": n / w2, "batches": s2.batches})
+        rates[f"{f:.2f}x"] = st
+    total_bytes = sum(ge.src.size for ge in batch.gens)
+    line = {"metric": "serving throughput req/s and p99 ms", "value": sat, "unit": "req/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"serving: {n} requests (half encode, half decode), shapes of the uneven "
+                                   "workload, Poisson arrivals, decode packets 20 us apart",
+                       "device_memory_budget": budget, "source_bytes": total_bytes},
+            "saturation_GBps_source": total_bytes / wall / 1e9, "rates": rates,
+            "plain_req_per_s": len(plain_reqs) / plain_wall, "round_trip_ok": ok,
+            "gpu_launches": srv.launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
+    ap.add_argument("--workload", choices=["uniform", "uneven", "serve"], default="uniform")
+    ap.add_argument("--gens", type=int, default=2048, help="generations of the uneven workload")
+    ap.add_argument("--requests", type=int, default=600, help="requests of the serving workload")
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -378,6 +519,10 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "uneven":
+        run_uneven(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
     else:
         run_gf(args, rank, world, local_rank)
     if world > 1 and args.impl == "gf":

@@ -1,0 +1,156 @@
+"""Uneven batched encode + decode (random linear network coding over a lossy
+channel), driven through the C ABI.
+
+Every generation g has its own field, generation size N_g and packet length
+len_g (section II: N source packets of len bytes, coding vectors drawn from
+GF(q)).  The sender encodes coded packets in the order of its coding-vector
+stream until the receiver holds N_g innovative packets; a packet is lost with
+the workload's erasure probability.  One step of the pipeline is:
+
+1. one persistent encode launch over every generation: the packets that
+   arrive are written contiguously into the receiver's buffer, the lost ones
+   into a discard buffer (the sender does the work for both);
+2. one batched decode over every generation from its received packets.
+
+Both launches come from plans, so a step is captured once in a CUDA graph and
+replayed.  How many packets the sender sends is fixed once, at set-up, by the
+library's own decode of the received coding vectors (the receiver's feedback:
+rank N reached after `used` received packets).
+
+The plain form does the same work with one encode call and one decode call
+per generation.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import gf, synth
+
+
+@dataclass
+class UnevenWork:
+    batch: synth.UnevenBatch
+    k_sent: list          # packets sent per generation
+    recv_rows: list       # stream indices of the received packets per generation
+    lost_rows: list       # stream indices of the lost packets per generation
+    dev: dict             # device tensors
+    enc_items: list       # encode descriptors (field, N, K, len, src, coef, out)
+    dec_items: list       # decode descriptors
+    bytes_src: int
+    bytes_coded: int
+
+
+def _cat(torch, arrays, dev):
+    flat = np.concatenate([a.reshape(-1) for a in arrays]) if arrays else np.zeros(1, np.uint8)
+    return torch.from_numpy(flat).to(dev)
+
+
+def build(batch: synth.UnevenBatch, device=None) -> UnevenWork:
+    """Upload a batch, fix the number of packets each sender sends, and
+    build the encode/decode descriptors of one step."""
+    import torch
+    dev = device or torch.device("cuda")
+    gens = batch.gens
+    # sender feedback: receiver rank over the received coding vectors
+    recv_all = [np.flatnonzero(~g.erased) for g in gens]
+    coef_recv = [np.ascontiguousarray(g.coef_stream[r]) for g, r in zip(gens, recv_all)]
+    c_dev = [torch.from_numpy(c.reshape(-1) if c.size else np.zeros(1, np.uint8)).to(dev) for c in coef_recv]
+    rank = torch.zeros(len(gens), dtype=torch.int32, device=dev)
+    used = torch.zeros(len(gens), dtype=torch.int32, device=dev)
+    items = [(g.field, g.n_src, c.shape[0], 0, cd, None, None, rank[i:i + 1], used[i:i + 1], None)
+             for i, (g, c, cd) in enumerate(zip(gens, coef_recv, c_dev))]
+    gf.gf_decode_batched(items)
+    torch.cuda.synchronize()
+    rank_h, used_h = rank.cpu().numpy(), used.cpu().numpy()
+    if (rank_h != np.array([g.n_src for g in gens])).any():
+        raise RuntimeError("a coding-vector stream is too short to reach rank N")
+    k_sent, recv_rows, lost_rows = [], [], []
+    for g, r, u in zip(gens, recv_all, used_h):
+        last = int(r[u - 1]) if u > 0 else -1
+        k = last + 1
+        k_sent.append(k)
+        sent = np.arange(k)
+        recv_rows.append(sent[~g.erased[:k]])
+        lost_rows.append(sent[g.erased[:k]])
+
+    # device buffers, one contiguous allocation per kind
+    src_off, rc_off, lc_off, rv_off, ls_off, out_off = [], [], [], [], [], []
+    s = rc = lc = rv = ls = 0
+    for g, rr, lr in zip(gens, recv_rows, lost_rows):
+        src_off.append(s); s += g.src.size
+        rc_off.append(rc); rc += rr.size * g.n_src
+        lc_off.append(lc); lc += lr.size * g.n_src
+        rv_off.append(rv); rv += rr.size * g.length
+        ls_off.append(ls); ls += lr.size * g.length
+    d = {
+        "src": _cat(torch, [g.src for g in gens], dev),
+        "coef_recv": _cat(torch, [g.coef_stream[r] for g, r in zip(gens, recv_rows)], dev),
+        "coef_lost": _cat(torch, [g.coef_stream[r] for g, r in zip(gens, lost_rows)], dev),
+        "recv": torch.zeros(max(rv, 1), dtype=torch.uint8, device=dev),
+        "lost": torch.zeros(max(ls, 1), dtype=torch.uint8, device=dev),
+        "out": torch.zeros(max(s, 1), dtype=torch.uint8, device=dev),
+        "rank": torch.zeros(len(gens), dtype=torch.int32, device=dev),
+        "used": torch.zeros(len(gens), dtype=torch.int32, device=dev),
+    }
+    base = {k: int(v.data_ptr()) for k, v in d.items()}
+    enc, dec = [], []
+    for i, (g, rr, lr) in enumerate(zip(gens, recv_rows, lost_rows)):
+        enc.append((g.field, g.n_src, rr.size, g.length, base["src"] + src_off[i], base["coef_recv"] + rc_off[i],
+                    base["recv"] + rv_off[i]))
+        enc.append((g.field, g.n_src, lr.size, g.length, base["src"] + src_off[i], base["coef_lost"] + lc_off[i],
+                    base["lost"] + ls_off[i]))
+        dec.append((g.field, g.n_src, rr.size, g.length, base["coef_recv"] + rc_off[i], base["recv"] + rv_off[i],
+                    base["out"] + src_off[i], base["rank"] + 4 * i, base["used"] + 4 * i, None))
+    d["_src_off"] = src_off
+    return UnevenWork(batch, k_sent, recv_rows, lost_rows, d, enc, dec, int(s), int(rv + ls))
+
+
+class UnevenStep:
+    """One step (encode launch + decode launches) as plans, optionally as a
+    CUDA graph."""
+
+    def __init__(self, work: UnevenWork, path: int = gf.PATH_AUTO):
+        self.work = work
+        self.enc = gf.Plan.encode(work.enc_items, path=path)
+        self.dec = gf.Plan.decode(work.dec_items)
+        self.graph = None
+
+    @property
+    def kernel_count(self) -> int:
+        return self.enc.kernel_count + self.dec.kernel_count
+
+    def launch(self, stream=None) -> None:
+        self.enc.launch(stream)
+        self.dec.launch(stream)
+
+    def capture(self, stream) -> None:
+        import torch
+        with torch.cuda.stream(stream):
+            self.launch(stream)  # warm-up outside capture
+            stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=stream):
+                self.launch(stream)
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def close(self) -> None:
+        self.enc.close()
+        self.dec.close()
+
+
+def plain_step(work: UnevenWork, gens=None, stream=None) -> None:
+    """The plain form: one encode call and one decode call per generation."""
+    idx = range(len(work.dec_items)) if gens is None else gens
+    for i in idx:
+        gf.gf_encode_batched([work.enc_items[2 * i], work.enc_items[2 * i + 1]], stream=stream)
+        gf.gf_decode_batched([work.dec_items[i]], stream=stream)
+
+
+def decoded(work: UnevenWork, i: int) -> np.ndarray:
+    g = work.batch.gens[i]
+    off = work.dev["_src_off"][i]
+    return work.dev["out"][off:off + g.src.size].cpu().numpy().reshape(g.n_src, g.length)
