@@ -161,7 +161,7 @@ __device__ __forceinline__ int find_gen(const long long *tile_start, int n_gens,
     return lo;
 }
 
-__global__ void __launch_bounds__(kEncThreads)
+__global__ void __launch_bounds__(kEncThreads, 2)
 encode_table_kernel(const EncGen *__restrict__ gens, const long long *__restrict__ tile_start, int n_gens,
                     long long total, WorkCounter *ctr)
 {
