@@ -34,7 +34,7 @@
 
 namespace gf {
 
-constexpr int kDecThreads = 256;
+constexpr int kDecThreads = 512;
 
 struct alignas(16) DecMap {
     ByteMap m;
@@ -95,25 +95,31 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     }
     __syncthreads();
 
-    // split of the new-row elimination: G pivot groups x nw words
-    const int G = max(1, min(N > 0 ? N : 1, kDecThreads / max(nw, 1)));
-
+    // coefficient words of the next arriving row, prefetched a row ahead
+    // (a thread owns coefficient word tid; N <= 4 * kDecThreads)
+    auto fetch = [&](int rr) -> uint32_t {
+        uint32_t v = 0;
+        if (rr < R && 4 * tid < N) {
+            const uint8_t *crow = g.coef + (size_t)rr * N;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (4 * tid + b < N) v |= (uint32_t)crow[4 * tid + b] << (8 * b);
+        }
+        return v;
+    };
+    uint32_t next = fetch(0);
     int r = 0;
     for (; r < R; ++r) {
         const int rank = s_rank;
         if (rank >= N) break;
-        // 1. load the arriving row: [coef | unit vector e_r]
-        const uint8_t *crow = g.coef + (size_t)r * N;
+        // 1. the arriving row: [coef | unit vector e_r]
+        const uint32_t mine = next;
+        next = fetch(r + 1);
         for (int j = tid; j < nw; j += blockDim.x) {
-            uint32_t v = 0;
+            uint32_t v = j == tid ? mine : 0u;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int k = 4 * j + b;
-                uint32_t e = 0;
-                if (k < N) e = crow[k];
-                else if (k == N + r) e = 1u;
-                v |= e << (8 * b);
-            }
+            for (int b = 0; b < 4; ++b)
+                if (4 * j + b == N + r) v |= 1u << (8 * b);
             cur[j] = v;
         }
         __syncthreads();
@@ -121,16 +127,29 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         for (int i = tid; i < N; i += blockDim.x) fsnap[i] = pivrow[i] >= 0 ? curb[i] : 0;
         __syncthreads();
         // 3. cur -= sum_p f_p * row(p): stored rows are reduced, so every f_p is
-        //    the arriving row's own value in column p
+        //    the arriving row's own value in column p.  Warp w takes the pivot
+        //    columns p = w (mod 8); each lane accumulates four word columns of a
+        //    128-word chunk in registers (independent chains), then one
+        //    atomicXor per word and warp combines the warps' partial sums.
         if (rank > 0) {
-            for (int idx = tid; idx < G * nw; idx += blockDim.x) {
-                const int grp = idx / nw, j = idx - grp * nw;
-                uint32_t acc = 0;
-                for (int pc = grp; pc < N; pc += G) {
+            for (int j0 = 0; j0 < nw; j0 += 128) {
+                uint32_t acc[4] = {0u, 0u, 0u, 0u};
+                for (int pc = warp; pc < N; pc += kDecThreads / 32) {
                     const uint32_t f = fsnap[pc];
-                    if (f) acc ^= apply_word(tab[f].m, rows[(size_t)pivrow[pc] * nw + j]);
+                    if (!f) continue;
+                    const ByteMap m = tab[f].m;
+                    const uint32_t *row = rows + (size_t)pivrow[pc] * nw;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j0 + lane + 32 * u;
+                        if (j < nw) acc[u] ^= apply_word(m, row[j]);
+                    }
                 }
-                if (acc) atomicXor(&cur[j], acc);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + lane + 32 * u;
+                    if (j < nw && acc[u]) atomicXor(&cur[j], acc[u]);
+                }
             }
         }
         __syncthreads();
@@ -170,13 +189,23 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         for (int s = tid; s < rank; s += blockDim.x)
             gsnap[s] = reinterpret_cast<const uint8_t *>(rows + (size_t)s * nw)[piv];
         __syncthreads();
-        // 7. back-substitution into the stored rows, 8. store the new row
-        for (int idx = tid; idx < rank * nw; idx += blockDim.x) {
-            const int s = idx / nw, j = idx - s * nw;
-            const uint32_t f = gsnap[s];
-            if (f) rows[(size_t)s * nw + j] ^= apply_word(tab[f].m, cur[j]);
+        // 7. back-substitution into the stored rows, 8. store the new row.
+        //    A thread owns a word column j (its prmt selectors computed once)
+        //    and walks a share of the stored rows.
+        {
+            const int per = max(1, kDecThreads / max(nw, 1));  // threads per column
+            const int cols = kDecThreads / per;
+            const int j_start = tid % cols, part = tid / cols;
+            for (int j = j_start; j < nw && part < per; j += cols) {
+                const uint32_t cw = cur[j];
+                const Sel sel = make_sel(cw);
+                for (int s = part; s < rank; s += per) {
+                    const uint32_t f = gsnap[s];
+                    if (f) rows[(size_t)s * nw + j] ^= apply(tab[f].m, sel);
+                }
+                if (part == 0) rows[(size_t)rank * nw + j] = cw;
+            }
         }
-        for (int j = tid; j < nw; j += blockDim.x) rows[(size_t)rank * nw + j] = cur[j];
         __syncthreads();
         if (tid == 0) {
             pivrow[piv] = rank;
