@@ -7,31 +7,33 @@
 // column j = c*x^j.  Eq. 2 over a whole generation therefore becomes one
 // binary matrix product:
 //     bit r of out_k[l] = sum_{i,j} bit_j(src_i[l]) * bit_r(c_ki * x^j)  (mod 2)
-// The tensor core computes the integer sum exactly (0/1 operands, sums below
-// 2^24 in FP32) and the parity is the result's lowest bit.  The kernel
-// computes the product transposed, one 128-byte column tile at a time:
+// The tensor core computes the integer sum exactly (0/1 operands, sums of
+// at most 512 terms, exact in the FP16 accumulator) and the parity is the
+// result's lowest bit.  The kernel computes the product transposed, one
+// 128-byte column tile at a time:
 //     D[l, 8k'+r] = sum_{(i,j)} A[l, 8i+j] * B[8i+j, 8k'+r]
 //   A (M = 128 byte positions x K = 8N source bits): written by the producer
 //     warps straight into tensor memory with tcgen05.st (one TMEM lane per
 //     byte position, 4 FP8 elements per column), no shared-memory traffic;
-//   B (K = 8N x N = 128 output bits of 16 coded packets): the coefficients'
+//   B (K = 8N x N = 256 output bits of 32 coded packets): the coefficients'
 //     bit matrices as FP8 0/1, K-major, 128-byte swizzled, resident in shared
-//     memory for the whole work item (N <= 64: 64 KB), copied from a 16 KB
+//     memory for the whole work item (N <= 64: 128 KB), copied from a 16 KB
 //     per-CTA table of the 256 possible 8x8 blocks;
-//   D (128 lanes x 128 FP32 columns), double-buffered in TMEM; the epilogue
-//     adds 2^23 (so the integer sum sits in the mantissa), takes bit 0 of
-//     each of the 8 values of a coded byte and packs them.
-// Work item = (generation, 16 coded packets); the CTA loops over all column
-// tiles of the item, one 128-byte column tile at a time, and each A fill
-// (128 positions x up to 64 sources) serves 32 coded packets: two MMA
-// streams of N = 128 into two D halves.  Roles, all running concurrently:
-// 2 warps publish the next item in a two-entry ring and build its B; 8
-// producer warps stage their source rows in shared memory with cp.async two
-// tiles ahead and fill A (double-buffered in TMEM); 1 thread issues the
-// MMAs; 16 epilogue warps drain the D halves.  Every mbarrier wait is bounded
-// by the global timer; a wait that gives up records GF_ETIMEOUT in the
-// library's device status word, the CTA drains its MMAs (bounded), frees
-// TMEM and exits.
+//   D (128 lanes x 256 FP16 columns): one N = 256 MMA stream per tile (full
+//     FP8 rate); the epilogue reads two columns per register
+//     (tcgen05.ld .pack::16b), adds 1024 so the integer sum sits in the
+//     mantissa, takes bit 0 of each of the 8 values of a coded byte and packs
+//     them.
+// Work item = (generation, 32 coded packets); the CTA loops over all column
+// tiles of the item.  Roles, all running concurrently: 2 warps publish the
+// next item in a two-entry ring and build its B; 8 producer warps stage
+// their source rows in shared memory with cp.async two tiles ahead and fill
+// A (double-buffered in TMEM, via a 2 KB table of pre-spread FP8 words);
+// 1 thread issues the MMAs; 16 epilogue warps drain D.  Every handshake
+// arrives once per warp (after __syncwarp), never once per thread.  Every
+// mbarrier wait is bounded by the global timer; a wait that gives up
+// records GF_ETIMEOUT in the library's device status word, the CTA drains
+// its MMAs (bounded), frees TMEM and exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,15 +53,14 @@ constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;  // warp 24
 constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25, 26
 constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 864
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
-constexpr int kCodedPerHalf = 16;   // coded packets per D half (MMA N = 128 output bits)
-constexpr int kCodedPerItem = 32;   // coded packets per work item (two D halves)
+constexpr int kCodedPerItem = 32;   // coded packets per work item (MMA N = 256 output bits)
 constexpr int kMaxSrc = 64;         // N limit of this path (A: 128 TMEM columns, B: 128 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
 constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte positions
 constexpr int kTmemCols = 512;
 constexpr int kABufCols = 128;      // A buffers at columns 0 and 128
-constexpr int kDCol0 = 256;         // D halves at columns 256 and 384
+constexpr int kDCol0 = 256;         // D: 256 columns from column 256
 constexpr uint32_t kOne = 0x38u;    // 1.0 in E4M3
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 constexpr uint32_t kSuspendNs = 100000;                 // try_wait suspend hint
@@ -70,10 +71,11 @@ constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 
 constexpr int kBBytes = 4 * kKBlock;        // 128 KB: B of one item (K <= 512)
 constexpr int kTabBytes = 256 * 8 * 8;      // 16 KB: 8x8 FP8 block of every coefficient
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
-constexpr int kSmemBytes = kBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*alignment slack*/;
+constexpr int kSpreadBytes = 256 * 8;       // 2 KB: the 8 FP8 bit values of every source byte
+constexpr int kSmemBytes = kBBytes + kTabBytes + kStageAll + kSpreadBytes + 1024 /*control*/ + 1024 /*slack*/;
 
 struct Ctl {
-    unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
+    unsigned long long a_full[2], a_empty[2], d_full, d_empty;
     unsigned long long info_full[2], info_empty[2], b_full, b_empty, drain;
     long long ring_item[2];
     uint32_t tmem_base;
@@ -180,6 +182,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
         : "memory");
 }
 
+// 32 lanes x 32 columns of 16-bit values, two adjacent columns per register
+__device__ __forceinline__ void tmem_ld16_pack(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.pack::16b.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -191,9 +205,12 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major,
-// N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(128 >> 3) << 17) |
+// Instruction descriptor, kind::f8f6f4: D = F16 (integer sums <= 512 are
+// exact), A = B = E4M3, both K-major, N = 256, M = 128.  An F16 accumulator
+// still takes one tensor-memory column per element (low 16 bits).  (N = 256 runs at the full FP8 rate whatever the commit
+// cadence; two N = 128 streams with commits between them run about a third
+// slower.)
+constexpr uint32_t kIdesc = (0u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(256 >> 3) << 17) |
                             ((uint32_t)(128 >> 4) << 24);
 
 // byte offset of 16-byte chunk m of K-block kb in row n (K-major, 128B swizzle)
@@ -207,6 +224,19 @@ __device__ __forceinline__ void spread_bits(uint32_t b, uint32_t &lo, uint32_t &
 {
     lo = (((b & 0xFu) * 0x00204081u) & 0x01010101u) * kOne;
     hi = (((b >> 4) * 0x00204081u) & 0x01010101u) * kOne;
+}
+
+// parity byte of 8 FP16 sums packed two per word (word j = output bits 2j,
+// 2j+1): adding 1024 puts the integer sum in the mantissa, so bit 0 of each
+// half is the parity
+__device__ __forceinline__ uint32_t parity_byte_h(const uint32_t *v)
+{
+    uint32_t h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h[j]) : "r"(v[j]), "r"(0x64006400u));
+    const uint32_t q0 = prmt(h[0], h[1], 0x6420u) & 0x01010101u;
+    const uint32_t q1 = prmt(h[2], h[3], 0x6420u) & 0x01010101u;
+    return ((q0 * 0x01020408u) >> 24) | (((q1 * 0x01020408u) >> 24) << 4);
 }
 
 // parity byte of 8 FP32 sums (columns 8k'..8k'+7 = output bits r = 0..7)
@@ -287,7 +317,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     unsigned char *Bs = smem;
     unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [c][r]
     unsigned char *staging = smem + kBBytes + kTabBytes;
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes + kStageAll);
+    uint2 *spread = reinterpret_cast<uint2 *>(smem + kBBytes + kTabBytes + kStageAll);  // [source byte]
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes + kStageAll + kSpreadBytes);
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
@@ -304,12 +335,17 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         }
         tab[e] = row;
     }
+    for (int b = tid; b < 256; b += blockDim.x) {
+        uint2 v;
+        spread_bits((uint32_t)b, v.x, v.y);
+        spread[b] = v;
+    }
     if (tid == 0) {
+        mbar_init(&ctl->d_full, 1);
+        mbar_init(&ctl->d_empty, kEpilogueWarps);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&ctl->a_full[b], kProducerWarps);
             mbar_init(&ctl->a_empty[b], 1);
-            mbar_init(&ctl->d_full[b], 1);
-            mbar_init(&ctl->d_empty[b], kEpilogueWarps / 2);
             mbar_init(&ctl->info_full[b], 1);
             mbar_init(&ctl->info_empty[b], kProducerWarps + kEpilogueWarps + 1);
         }
@@ -453,7 +489,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     }
                     uint32_t v[16];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) spread_bits(b[t], v[2 * t], v[2 * t + 1]);
+                    for (int t = 0; t < 8; ++t) {
+                        const uint2 w = spread[b[t]];
+                        v[2 * t] = w.x;
+                        v[2 * t + 1] = w.y;
+                    }
                     tmem_st16(acol + grp * 16, v);
                 }
                 tmem_wait_st();
@@ -468,9 +508,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     } else if (warp < kProducerWarps + kEpilogueWarps) {
         // ---------------- epilogue: 64 D columns -> parity bytes -> global ----------------
         const int quarter = warp & 3;
-        const int sub = (warp - kProducerWarps) >> 2;   // 0..3
-        const int half = sub >> 1;                       // D half
-        const int oct = sub & 1;                         // 8-packet group inside the half
+        const int oct = (warp - kProducerWarps) >> 2;   // 8-packet group of the item: 0..3
         const int pos = quarter * 32 + lane;
         uint32_t tiles = 0;
         for (uint32_t seq = 0;; ++seq) {
@@ -485,31 +523,32 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item < 0) break;
             const int gi = locate(tile_start, n_gens, item);
             const EncGen g = gens[gi];
-            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + half * kCodedPerHalf + oct * 8;
+            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + oct * 8;
             const int K = g.n_coded;
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
             bool ok = true;
             for (int ct = 0; ct < ncols; ++ct) {
-                if (!mbar_wait_warp(&ctl->d_full[half], tiles & 1u, abort_flag)) {
+                if (!mbar_wait_warp(&ctl->d_full, tiles & 1u, abort_flag)) {
                     ctl->abort = 1;
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + half * 128 + oct * 64;
-                uint32_t outb[8];
-#pragma unroll
-                for (int g2 = 0; g2 < 2; ++g2) {
-                    uint32_t v[32];
-                    tmem_ld32(dcol + g2 * 32, v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) outb[g2 * 4 + t] = parity_byte(v + 8 * t);
-                }
+                const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + oct * 64;
+                uint32_t va[16], vb[16];
+                tmem_ld16_pack(dcol, va);
+                tmem_ld16_pack(dcol + 32, vb);
+                tmem_wait_ld();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&ctl->d_empty[half]);
+                if (lane == 0) mbar_arrive(&ctl->d_empty);  // D is free as soon as it is in registers
+                uint32_t outb[8];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    outb[t] = parity_byte_h(va + 4 * t);
+                    outb[4 + t] = parity_byte_h(vb + 4 * t);
+                }
                 const unsigned long long col = (unsigned long long)ct * kColTile + pos;
                 if (col < len) {
                     uint8_t *o = g.out + (size_t)k0 * len + col;
@@ -537,8 +576,6 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const EncGen g = gens[gi];
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const int ksteps = (g.n_src + 3) / 4;  // 4 sources = 32 FP8 per MMA
-            const int k_item = g.n_coded - (int)(item - __ldg(tile_start + gi)) * kCodedPerItem;
-            const int halves = k_item > kCodedPerHalf ? 2 : 1;
             bool ok = mbar_wait(&ctl->b_full, seq & 1u, abort_flag);
             tc_fence_after();
             const uint64_t bdesc0 = b_desc(smem_u32(Bs));
@@ -548,36 +585,23 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     ok = false;
                     break;
                 }
+                if (!mbar_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                for (int h = 0; h < halves; ++h) {
-                    if (!mbar_wait(&ctl->d_empty[h], (tiles & 1u) ^ 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
-                    // B lies below 256 KB of shared memory)
-                    const uint64_t dh = bdesc0 + (uint64_t)((h * (128 * 128)) >> 4);
-                    const uint32_t dt = tmem + kDCol0 + h * 128;
-                    const uint32_t at = tmem + buf * kABufCols;
-                    tc_mma(dt, at, dh, kIdesc, 0u);
+                // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
+                // B lies below 256 KB of shared memory)
+                const uint32_t dt = tmem + kDCol0;
+                const uint32_t at = tmem + buf * kABufCols;
+                tc_mma(dt, at, bdesc0, kIdesc, 0u);
 #pragma unroll
-                    for (int s = 1; s < 16; ++s) {
-                        if (s < ksteps)
-                            tc_mma(dt, at + s * 8, dh + (uint64_t)((((s * 32) >> 7) * kKBlock + ((s * 32) & 127)) >> 4),
-                                   kIdesc, 1u);
-                    }
-                    tc_commit(&ctl->d_full[h]);
+                for (int s = 1; s < 16; ++s) {
+                    if (s < ksteps)
+                        tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)((((s * 32) >> 7) * kKBlock + ((s * 32) & 127)) >> 4),
+                               kIdesc, 1u);
                 }
-                if (!ok) break;
-                if (halves == 1) {
-                    // keep both halves' phases in step: the idle half completes an empty phase
-                    if (!mbar_wait(&ctl->d_empty[1], (tiles & 1u) ^ 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_commit(&ctl->d_full[1]);
-                }
+                tc_commit(&ctl->d_full);
                 tc_commit(&ctl->a_empty[buf]);
                 ++fills;
                 ++tiles;
