@@ -315,7 +315,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Bs = smem;
-    unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [c][r]
+    unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [r][c]
     unsigned char *staging = smem + kBBytes + kTabBytes;
     uint2 *spread = reinterpret_cast<uint2 *>(smem + kBBytes + kTabBytes + kStageAll);  // [source byte]
     Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes + kStageAll + kSpreadBytes);
@@ -324,9 +324,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // the 8x8 FP8 block of every coefficient: row r, byte j = bit r of c*x^j
+    // the 8x8 FP8 block of every coefficient: row r, byte j = bit r of c*x^j,
+    // stored [r][c] so that lanes looking up different coefficients for the
+    // same row spread over all shared-memory banks
     for (int e = tid; e < 256 * 8; e += blockDim.x) {
-        const uint32_t c = (uint32_t)e >> 3, r = (uint32_t)e & 7u;
+        const uint32_t c = (uint32_t)e & 255u, r = (uint32_t)e >> 8;
         uint32_t p = c;
         unsigned long long row = 0;
         for (int j = 0; j < 8; ++j) {
@@ -412,8 +414,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     const bool live = kbase + kp < K;
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
-                        const unsigned long long v0 = live ? tab[(cc[t] & 0xFFu) * 8 + r] : 0ull;
-                        const unsigned long long v1 = live ? tab[(cc[t] >> 8) * 8 + r] : 0ull;
+                        const unsigned long long v0 = live ? tab[r * 256 + (cc[t] & 0xFFu)] : 0ull;
+                        const unsigned long long v1 = live ? tab[r * 256 + (cc[t] >> 8)] : 0ull;
                         uint4 q;
                         q.x = (uint32_t)v0;
                         q.y = (uint32_t)(v0 >> 32);
