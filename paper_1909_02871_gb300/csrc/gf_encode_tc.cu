@@ -48,10 +48,10 @@ namespace tc {
 
 constexpr int kProducerWarps = 8;   // 2 per TMEM lane quarter, 32 sources each
 constexpr int kEpilogueWarps = 16;  // 4 per lane quarter, 8 coded packets each
-constexpr int kBWarps = 2;          // coefficient bit matrices (B)
+constexpr int kBWarps = 4;          // coefficient bit matrices (B)
 constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;  // warp 24
-constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25, 26
-constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 864
+constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
+constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerItem = 32;   // coded packets per work item (MMA N = 256 output bits)
 constexpr int kMaxSrc = 64;         // N limit of this path (A: 128 TMEM columns, B: 128 KB)
@@ -374,7 +374,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int bt = tid - kBWarp0 * 32;
         const int m = bt & 7;            // 16-byte chunk in a K-block: sources 2m, 2m+1
         const int kb = (bt >> 3) & 3;    // K-block: sources 16kb .. 16kb+15
-        const int kq0 = bt >> 5;         // coded-packet octets kq0, kq0 + 2
+        const int kq0 = bt >> 5;         // coded-packet octet kq0 (0..3)
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (bt == 0) {
@@ -394,10 +394,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
             const int nkb = (N + 15) / 16;
             const int i0 = 16 * kb + 2 * m, i1 = i0 + 1;
-            uint32_t cc[16];  // coefficient pair (c[k][i0], c[k][i1]) packed in 16 bits
+            uint32_t cc[8];  // coefficient pair (c[k][i0], c[k][i1]) packed in 16 bits
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int k = kbase + (kq0 + 2 * (t >> 3)) * 8 + (t & 7);
+            for (int t = 0; t < 8; ++t) {
+                const int k = kbase + kq0 * 8 + t;
                 const uint32_t a = (kb < nkb && k < K && i0 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i0) : 0u;
                 const uint32_t b = (kb < nkb && k < K && i1 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i1) : 0u;
                 cc[t] = a | (b << 8);
@@ -409,8 +409,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
             if (kb < nkb) {
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int kp = (kq0 + 2 * (t >> 3)) * 8 + (t & 7);
+                for (int t = 0; t < 8; ++t) {
+                    const int kp = kq0 * 8 + t;
                     const bool live = kbase + kp < K;
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
