@@ -1,5 +1,6 @@
 // gf_encode_tc.cu -- bit-sliced GF(256) generation encode on the sm_103a
-// tensor cores (tcgen05, kind::f8f6f4, FP32 accumulators in TMEM).
+// tensor cores (tcgen05 kind::mxf4 block-scaled MMA, FP32 accumulators in
+// TMEM).
 //
 // The imul algorithm of section IV-B rests on the identity
 //     c * a = XOR_j a_j * (c * x^j),        a_j = bit j of a,
@@ -7,28 +8,30 @@
 // column j = c*x^j.  Eq. 2 over a whole generation therefore becomes one
 // binary matrix product:
 //     bit r of out_k[l] = sum_{i,j} bit_j(src_i[l]) * bit_r(c_ki * x^j)  (mod 2)
-// The tensor core computes the integer sum exactly (0/1 operands, sums of
-// at most 512 terms, exact in the FP16 accumulator) and the parity is the
-// result's lowest bit.  The kernel computes the product transposed, one
-// 128-byte column tile at a time:
-//     D[l, 8k'+r] = sum_{(i,j)} A[l, 8i+j] * B[8i+j, 8k'+r]
+// The tensor core computes the integer sum exactly (0/1 operands, at most
+// 512 terms) and the parity is the result's lowest bit.  The operands are
+// E2M1 (4-bit) values 0 and 1.0 with every block scale 1.0 (UE8M0 127),
+// which runs at twice the FP8 rate.  The kernel computes the product
+// transposed, one 128-byte column tile at a time:
+//     D[l, 8k'+r] = 2^23 + sum_{(i,j)} A[l, 8i+j] * B[8i+j, 8k'+r]
 //   A (M = 128 byte positions x K = 8N source bits): written by the producer
 //     warps straight into tensor memory with tcgen05.st (one TMEM lane per
-//     byte position, 4 FP8 elements per column), no shared-memory traffic;
+//     byte position, one column = the 8 bit values of one source byte);
 //   B (K = 8N x N = 256 output bits of 32 coded packets): the coefficients'
-//     bit matrices as FP8 0/1, K-major, 128-byte swizzled, resident in shared
-//     memory for the whole work item (N <= 64: 128 KB), copied from a 16 KB
-//     per-CTA table of the 256 possible 8x8 blocks;
-//   D (128 lanes x 256 FP16 columns): one N = 256 MMA stream per tile (full
-//     FP8 rate); the epilogue reads two columns per register
-//     (tcgen05.ld .pack::16b), adds 1024 so the integer sum sits in the
-//     mantissa, takes bit 0 of each of the 8 values of a coded byte and packs
-//     them.
+//     bit matrices, K-major, 128-byte swizzled, double-buffered in shared
+//     memory (N <= 64: 64 KB each), built from an 8 KB per-CTA table of the
+//     256 possible 8x8 blocks;
+//   D (128 lanes x 256 FP32 columns): one N = 256 MMA stream per tile.  The
+//     first MMA of a tile is a rank-1 product with block scale 2^23 that sets
+//     every element to 2^23; the sum then sits in the low mantissa bits
+//     (exact: ulp(2^23) = 1), so the epilogue reads only the low 16 bits of
+//     each column (tcgen05.ld .pack::16b, two columns per register), takes
+//     bit 0 of each of the 8 values of a coded byte and packs them.
 // Work item = (generation, 32 coded packets); the CTA loops over all column
-// tiles of the item.  Roles, all running concurrently: 2 warps publish the
+// tiles of the item.  Roles, all running concurrently: 4 warps publish the
 // next item in a two-entry ring and build its B; 8 producer warps stage
 // their source rows in shared memory with cp.async two tiles ahead and fill
-// A (double-buffered in TMEM, via a 2 KB table of pre-spread FP8 words);
+// A (double-buffered in TMEM, via a 1 KB table of pre-spread words);
 // 1 thread issues the MMAs; 16 epilogue warps drain D.  Every handshake
 // arrives once per warp (after __syncwarp), never once per thread.  Every
 // mbarrier wait is bounded by the global timer; a wait that gives up
@@ -54,29 +57,38 @@ constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
 constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerItem = 32;   // coded packets per work item (MMA N = 256 output bits)
-constexpr int kMaxSrc = 64;         // N limit of this path (A: 128 TMEM columns, B: 128 KB)
+constexpr int kMaxSrc = 64;         // N limit of this path (A: 64 TMEM columns, B: 64 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
 constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte positions
+// tensor memory columns (all 512 allocated)
 constexpr int kTmemCols = 512;
-constexpr int kABufCols = 128;      // A buffers at columns 0 and 128
+constexpr int kABufCols = 64;       // A buffers at columns 0 and 64 (one column per source)
+constexpr int kBiasACol = 128;      // rank-1 bias operand: element 0 = 1.0, 8 columns
+constexpr int kSfOneA = 160;        // block scales 1.0 (UE8M0 127) for A, 32 columns
+constexpr int kSfOneB = 192;        // block scales 1.0 for B, 32 columns
+constexpr int kSfBiasA = 224;       // block scales 2^23 (UE8M0 150) for the bias MMA, 32 columns
 constexpr int kDCol0 = 256;         // D: 256 columns from column 256
-constexpr uint32_t kOne = 0x38u;    // 1.0 in E4M3
+constexpr uint32_t kOne = 0x2u;     // 1.0 in E2M1
+constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;   // four UE8M0 scales 2^0
+constexpr uint32_t kScaleBias = 0x96969696u;  // four UE8M0 scales 2^23
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
 constexpr uint32_t kSuspendNs = 100000;                 // try_wait suspend hint
 constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
-constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes
-constexpr int kBBytes = 4 * kKBlock;        // 128 KB: B of one item (K <= 512)
-constexpr int kTabBytes = 256 * 8 * 8;      // 16 KB: 8x8 FP8 block of every coefficient
+constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
+constexpr int kBBytes = 2 * kKBlock;        // 64 KB: B of one item (K <= 512)
+constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
+constexpr int kTabBytes = 256 * 8 * 4;      // 8 KB: 8x8 E2M1 block of every coefficient
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
-constexpr int kSpreadBytes = 256 * 8;       // 2 KB: the 8 FP8 bit values of every source byte
-constexpr int kSmemBytes = kBBytes + kTabBytes + kStageAll + kSpreadBytes + 1024 /*control*/ + 1024 /*slack*/;
+constexpr int kSpreadBytes = 256 * 4;       // 1 KB: the 8 E2M1 bit values of every source byte
+constexpr int kSmemBytes =
+    2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + kSpreadBytes + 1024 /*control*/ + 1024 /*slack*/;
 
 struct Ctl {
     unsigned long long a_full[2], a_empty[2], d_full, d_empty;
-    unsigned long long info_full[2], info_empty[2], b_full, b_empty, drain;
+    unsigned long long info_full[2], info_empty[2], b_full[2], b_empty[2], drain;
     long long ring_item[2];
     uint32_t tmem_base;
     int abort;
@@ -147,15 +159,27 @@ __device__ __forceinline__ void tc_commit(unsigned long long *bar)
                  : "memory");
 }
 
-// D[tmem] (+)= A[tmem] * B[smem]
+// D[tmem] (+)= (A[tmem] x scale_A) * (B[smem] x scale_B); E2M1 operands,
+// UE8M0 block scales (one per 32 K elements) read from tensor memory
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                       uint32_t accumulate)
+                                       uint32_t sf_a, uint32_t sf_b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(sf_a), "r"(sf_b), "r"(accumulate)
+        : "memory");
+}
+
+// 32 lanes x 16 columns of one value
+__device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(v)
         : "memory");
 }
 
@@ -166,19 +190,6 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         "%15, %16};" ::"r"(taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
         "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
         : "memory");
 }
 
@@ -205,48 +216,27 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor, kind::f8f6f4: D = F16 (integer sums <= 512 are
-// exact), A = B = E4M3, both K-major, N = 256, M = 128.  An F16 accumulator
-// still takes one tensor-memory column per element (low 16 bits).  (N = 256 runs at the full FP8 rate whatever the commit
-// cadence; two N = 128 streams with commits between them run about a third
-// slower.)
-constexpr uint32_t kIdesc = (0u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(256 >> 3) << 17) |
+// Instruction descriptor, kind::mxf4 block-scaled: A = B = E2M1 (format 1),
+// both K-major, N = 256, scale type UE8M0 (bit 23), M = 128, scale-factor
+// ids 0, dense K = 64.  D is FP32.
+constexpr uint32_t kIdesc = (0u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) | (1u << 23) |
                             ((uint32_t)(128 >> 4) << 24);
 
-// byte offset of 16-byte chunk m of K-block kb in row n (K-major, 128B swizzle)
-__device__ __forceinline__ uint32_t b_chunk_offset(int n, int kb, int m)
+// the 8 E2M1 values (nibbles j = 0..7) of one source byte: 1.0 where bit j is set
+__host__ __device__ __forceinline__ uint32_t spread_bits(uint32_t b)
 {
-    return (uint32_t)(kb * (128 * 128) + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
+    uint32_t w = 0;
+    for (int j = 0; j < 8; ++j)
+        if ((b >> j) & 1u) w |= kOne << (4 * j);
+    return w;
 }
 
-// 8 FP8 values (bytes j = 0..7) of one source byte: 1.0 where bit j is set
-__device__ __forceinline__ void spread_bits(uint32_t b, uint32_t &lo, uint32_t &hi)
-{
-    lo = (((b & 0xFu) * 0x00204081u) & 0x01010101u) * kOne;
-    hi = (((b >> 4) * 0x00204081u) & 0x01010101u) * kOne;
-}
-
-// parity byte of 8 FP16 sums packed two per word (word j = output bits 2j,
-// 2j+1): adding 1024 puts the integer sum in the mantissa, so bit 0 of each
-// half is the parity
-__device__ __forceinline__ uint32_t parity_byte_h(const uint32_t *v)
-{
-    uint32_t h[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) asm("add.rn.f16x2 %0, %1, %2;" : "=r"(h[j]) : "r"(v[j]), "r"(0x64006400u));
-    const uint32_t q0 = prmt(h[0], h[1], 0x6420u) & 0x01010101u;
-    const uint32_t q1 = prmt(h[2], h[3], 0x6420u) & 0x01010101u;
-    return ((q0 * 0x01020408u) >> 24) | (((q1 * 0x01020408u) >> 24) << 4);
-}
-
-// parity byte of 8 FP32 sums (columns 8k'..8k'+7 = output bits r = 0..7)
+// parity byte of 8 biased sums, low 16 bits packed two per word (word j =
+// output bits 2j, 2j+1): bit 0 of each half is the parity of that sum
 __device__ __forceinline__ uint32_t parity_byte(const uint32_t *v)
 {
-    uint32_t w[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) w[r] = __float_as_uint(__uint_as_float(v[r]) + 8388608.0f);
-    const uint32_t q0 = prmt(prmt(w[0], w[1], 0x0040u), prmt(w[2], w[3], 0x0040u), 0x5410u) & 0x01010101u;
-    const uint32_t q1 = prmt(prmt(w[4], w[5], 0x0040u), prmt(w[6], w[7], 0x0040u), 0x5410u) & 0x01010101u;
+    const uint32_t q0 = prmt(v[0], v[1], 0x6420u) & 0x01010101u;
+    const uint32_t q1 = prmt(v[2], v[3], 0x6420u) & 0x01010101u;
     return ((q0 * 0x01020408u) >> 24) | (((q1 * 0x01020408u) >> 24) << 4);
 }
 
@@ -314,33 +304,35 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *Bs = smem;
-    unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + kBBytes);  // [r][c]
-    unsigned char *staging = smem + kBBytes + kTabBytes;
-    uint2 *spread = reinterpret_cast<uint2 *>(smem + kBBytes + kTabBytes + kStageAll);  // [source byte]
-    Ctl *ctl = reinterpret_cast<Ctl *>(smem + kBBytes + kTabBytes + kStageAll + kSpreadBytes);
+    unsigned char *Bs = smem;                                // two B buffers
+    unsigned char *bias_b = smem + 2 * kBBytes;
+    uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][c]
+    unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
+    uint32_t *spread = reinterpret_cast<uint32_t *>(staging + kStageAll);  // [source byte]
+    Ctl *ctl = reinterpret_cast<Ctl *>(reinterpret_cast<unsigned char *>(spread) + kSpreadBytes);
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // the 8x8 FP8 block of every coefficient: row r, byte j = bit r of c*x^j,
-    // stored [r][c] so that lanes looking up different coefficients for the
-    // same row spread over all shared-memory banks
+    // the 8x8 E2M1 block of every coefficient: row r, nibble j = bit r of
+    // c*x^j, stored [r][c] so that lanes looking up different coefficients
+    // for the same row spread over all shared-memory banks
     for (int e = tid; e < 256 * 8; e += blockDim.x) {
         const uint32_t c = (uint32_t)e & 255u, r = (uint32_t)e >> 8;
-        uint32_t p = c;
-        unsigned long long row = 0;
+        uint32_t p = c, row = 0;
         for (int j = 0; j < 8; ++j) {
-            if ((p >> r) & 1u) row |= (unsigned long long)kOne << (8 * j);
+            if ((p >> r) & 1u) row |= kOne << (4 * j);
             p = xtime(8, p);
         }
         tab[e] = row;
     }
-    for (int b = tid; b < 256; b += blockDim.x) {
-        uint2 v;
-        spread_bits((uint32_t)b, v.x, v.y);
-        spread[b] = v;
+    for (int v = tid; v < 256; v += blockDim.x) spread[v] = spread_bits((uint32_t)v);
+    // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
+    for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x) {
+        const int n = e >> 3, phys = e & 7;
+        const uint32_t first = ((phys ^ (n & 7)) == 0) ? kOne : 0u;
+        *reinterpret_cast<uint4 *>(bias_b + 16 * e) = make_uint4(first, 0u, 0u, 0u);
     }
     if (tid == 0) {
         mbar_init(&ctl->d_full, 1);
@@ -350,9 +342,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             mbar_init(&ctl->a_empty[b], 1);
             mbar_init(&ctl->info_full[b], 1);
             mbar_init(&ctl->info_empty[b], kProducerWarps + kEpilogueWarps + 1);
+            mbar_init(&ctl->b_full[b], 1);
+            mbar_init(&ctl->b_empty[b], 1);
         }
-        mbar_init(&ctl->b_full, 1);
-        mbar_init(&ctl->b_empty, 1);
         mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -364,17 +356,37 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // bias operand -> tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
+    // constant tensor-memory operands: bias A (element 0 = 1.0) and the
+    // block-scale columns, written by one warp per lane quarter
+    if (warp >= kProducerWarps && warp < kProducerWarps + 4) {
+        const uint32_t q = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        uint32_t v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0u;
+        v[0] = kOne;
+        tmem_st16(q + kBiasACol, v);
+        for (int c = 0; c < 32; c += 16) {
+            tmem_fill16(q + kSfOneA + c, kScaleOne);
+            tmem_fill16(q + kSfOneB + c, kScaleOne);
+            tmem_fill16(q + kSfBiasA + c, kScaleBias);
+        }
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp >= kBWarp0) {
         // ------------- B builder: publishes the next item, then its bit matrices -------------
         const int bt = tid - kBWarp0 * 32;
-        const int m = bt & 7;            // 16-byte chunk in a K-block: sources 2m, 2m+1
-        const int kb = (bt >> 3) & 3;    // K-block: sources 16kb .. 16kb+15
-        const int kq0 = bt >> 5;         // coded-packet octet kq0 (0..3)
+        const int m = bt & 7;            // 16-byte chunk of a K-block: sources 4m .. 4m+3
+        const int kb = (bt >> 3) & 1;    // K-block: sources 32kb .. 32kb+31
+        const int kq = bt >> 4;          // coded packets 4kq .. 4kq+3 of the item
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (bt == 0) {
@@ -392,42 +404,44 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const EncGen g = gens[gi];
             const int kbase = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem;
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
-            const int nkb = (N + 15) / 16;
-            const int i0 = 16 * kb + 2 * m, i1 = i0 + 1;
-            uint32_t cc[8];  // coefficient pair (c[k][i0], c[k][i1]) packed in 16 bits
+            const int nkb = (N + 31) / 32;
+            const int i0 = 32 * kb + 4 * m;
+            uint32_t cc[4];  // coefficients c[k][i0 .. i0+3], one byte each
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int k = kbase + kq0 * 8 + t;
-                const uint32_t a = (kb < nkb && k < K && i0 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i0) : 0u;
-                const uint32_t b = (kb < nkb && k < K && i1 < N) ? (uint32_t)__ldg(g.coef + (size_t)k * ld + i1) : 0u;
-                cc[t] = a | (b << 8);
+            for (int t = 0; t < 4; ++t) {
+                const int k = kbase + kq * 4 + t;
+                uint32_t w = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (kb < nkb && k < K && i0 + u < N) w |= (uint32_t)__ldg(g.coef + (size_t)k * ld + i0 + u) << (8 * u);
+                cc[t] = w;
             }
-            // B is single-buffered: wait until the MMAs of the previous item are done
+            // wait until the MMAs of the item two back are done with this buffer
+            unsigned char *Bb = Bs + e * kBBytes;
             bool ok = true;
-            if (bt == 0) ok = mbar_wait(&ctl->b_empty, (seq & 1u) ^ 1u, abort_flag);
+            if (bt == 0) ok = mbar_wait(&ctl->b_empty[e], (use & 1u) ^ 1u, abort_flag);
             if (bt == 0 && !ok) ctl->abort = 1;
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
             if (kb < nkb) {
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int kp = kq0 * 8 + t;
-                    const bool live = kbase + kp < K;
+                for (int t = 0; t < 4; ++t) {
+                    const int kp = kq * 4 + t;
+                    const uint32_t w = cc[t];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
-                        const unsigned long long v0 = live ? tab[r * 256 + (cc[t] & 0xFFu)] : 0ull;
-                        const unsigned long long v1 = live ? tab[r * 256 + (cc[t] >> 8)] : 0ull;
+                        const uint32_t *tr = tab + r * 256;
                         uint4 q;
-                        q.x = (uint32_t)v0;
-                        q.y = (uint32_t)(v0 >> 32);
-                        q.z = (uint32_t)v1;
-                        q.w = (uint32_t)(v1 >> 32);
-                        *reinterpret_cast<uint4 *>(Bs + b_chunk(8 * kp + r, kb, m)) = q;
+                        q.x = tr[w & 0xFFu];
+                        q.y = tr[(w >> 8) & 0xFFu];
+                        q.z = tr[(w >> 16) & 0xFFu];
+                        q.w = tr[w >> 24];
+                        *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, kb, m)) = q;
                     }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
-            if (bt == 0) mbar_arrive(&ctl->b_full);
+            if (bt == 0) mbar_arrive(&ctl->b_full[e]);
             if (*abort_flag) break;
         }
     } else if (warp < kProducerWarps) {
@@ -478,25 +492,24 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     break;
                 }
                 tc_fence_after();
-                const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 64;
+                const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 32;
                 const unsigned char *sb = stage + (ct % kStages) * kStageBytes + lane;
 #pragma unroll
-                for (int grp = 0; grp < 4; ++grp) {
-                    uint32_t b[8];
-                    if (staged) {
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) b[t] = sb[(grp * 8 + t) * 32];
-                    } else {
-                        load_direct(g, ibase, (unsigned long long)ct * kColTile + pos, b, grp);
-                    }
+                for (int half = 0; half < 2; ++half) {
                     uint32_t v[16];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const uint2 w = spread[b[t]];
-                        v[2 * t] = w.x;
-                        v[2 * t + 1] = w.y;
+                    for (int grp = 0; grp < 2; ++grp) {
+                        uint32_t b[8];
+                        if (staged) {
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) b[t] = sb[((2 * half + grp) * 8 + t) * 32];
+                        } else {
+                            load_direct(g, ibase, (unsigned long long)ct * kColTile + pos, b, 2 * half + grp);
+                        }
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread[b[t]];
                     }
-                    tmem_st16(acol + grp * 16, v);
+                    tmem_st16(acol + half * 16, v);
                 }
                 tmem_wait_st();
                 tc_fence_before();
@@ -548,8 +561,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 uint32_t outb[8];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    outb[t] = parity_byte_h(va + 4 * t);
-                    outb[4 + t] = parity_byte_h(vb + 4 * t);
+                    outb[t] = parity_byte(va + 4 * t);
+                    outb[4 + t] = parity_byte(vb + 4 * t);
                 }
                 const unsigned long long col = (unsigned long long)ct * kColTile + pos;
                 if (col < len) {
@@ -565,6 +578,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     } else if (lane == 0) {
         // ---------------- MMA issuer (warp kMmaWarp, one thread) ----------------
         uint32_t fills = 0, tiles = 0;
+        const uint64_t bias_desc = b_desc(smem_u32(bias_b));
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (!mbar_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
@@ -577,10 +591,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int gi = locate(tile_start, n_gens, item);
             const EncGen g = gens[gi];
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
-            const int ksteps = (g.n_src + 3) / 4;  // 4 sources = 32 FP8 per MMA
-            bool ok = mbar_wait(&ctl->b_full, seq & 1u, abort_flag);
+            const int ksteps = (g.n_src + 7) / 8;  // 8 sources = 64 E2M1 values per MMA
+            bool ok = mbar_wait(&ctl->b_full[e], use & 1u, abort_flag);
             tc_fence_after();
-            const uint64_t bdesc0 = b_desc(smem_u32(Bs));
+            const uint64_t bdesc0 = b_desc(smem_u32(Bs + e * kBBytes));
             for (int ct = 0; ct < ncols && ok; ++ct) {
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
                 if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
@@ -596,19 +610,19 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 // B lies below 256 KB of shared memory)
                 const uint32_t dt = tmem + kDCol0;
                 const uint32_t at = tmem + buf * kABufCols;
-                tc_mma(dt, at, bdesc0, kIdesc, 0u);
+                tc_mma(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
 #pragma unroll
-                for (int s = 1; s < 16; ++s) {
+                for (int s = 0; s < 8; ++s) {
                     if (s < ksteps)
-                        tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)((((s * 32) >> 7) * kKBlock + ((s * 32) & 127)) >> 4),
-                               kIdesc, 1u);
+                        tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
+                               tmem + kSfOneA, tmem + kSfOneB, 1u);
                 }
                 tc_commit(&ctl->d_full);
                 tc_commit(&ctl->a_empty[buf]);
                 ++fills;
                 ++tiles;
             }
-            tc_commit(&ctl->b_empty);
+            tc_commit(&ctl->b_empty[e]);
             if (!ok) {
                 ctl->abort = 1;
                 break;
