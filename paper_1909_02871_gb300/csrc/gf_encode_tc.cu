@@ -90,6 +90,8 @@ struct Ctl {
     unsigned long long a_full[2], a_empty[2], d_full, d_empty;
     unsigned long long info_full[2], info_empty[2], b_full[2], b_empty[2], drain;
     long long ring_item[2];
+    EncGen ring_gen[2];  // generation record of each published item
+    int ring_k0[2];      // its first coded packet
     uint32_t tmem_base;
     int abort;
 };
@@ -394,15 +396,19 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 long long it = ok ? (long long)atomicAdd(&ctr->next, 1ull) : kSentinel;
                 if (it >= total) it = kSentinel;
                 if (!ok) ctl->abort = 1;
+                if (it != kSentinel) {
+                    const int gi = locate(tile_start, n_gens, it);
+                    ctl->ring_gen[e] = gens[gi];
+                    ctl->ring_k0[e] = (int)(it - __ldg(tile_start + gi)) * kCodedPerItem;
+                }
                 ring[e] = it;
                 mbar_arrive(&ctl->info_full[e]);
             }
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
             const long long item = ring[e];
             if (item == kSentinel) break;
-            const int gi = locate(tile_start, n_gens, item);
-            const EncGen g = gens[gi];
-            const int kbase = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem;
+            const EncGen g = ctl->ring_gen[e];
+            const int kbase = ctl->ring_k0[e];
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
             const int nkb = (N + 31) / 32;
             const int i0 = 32 * kb + 4 * m;
@@ -459,11 +465,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 break;
             }
             const long long item = ring[e];
+            const EncGen g = ctl->ring_gen[e];
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int gi = locate(tile_start, n_gens, item);
-            const EncGen g = gens[gi];
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
             if (staged) {
@@ -533,12 +538,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 break;
             }
             const long long item = ring[e];
+            const EncGen g = ctl->ring_gen[e];
+            const int k0 = ctl->ring_k0[e] + oct * 8;
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int gi = locate(tile_start, n_gens, item);
-            const EncGen g = gens[gi];
-            const int k0 = (int)(item - __ldg(tile_start + gi)) * kCodedPerItem + oct * 8;
             const int K = g.n_coded;
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
@@ -586,10 +590,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 break;
             }
             const long long item = ring[e];
+            const EncGen g = ctl->ring_gen[e];
             mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int gi = locate(tile_start, n_gens, item);
-            const EncGen g = gens[gi];
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const int ksteps = (g.n_src + 7) / 8;  // 8 sources = 64 E2M1 values per MMA
             bool ok = mbar_wait(&ctl->b_full[e], use & 1u, abort_flag);
