@@ -178,7 +178,7 @@ def run_gf(args, rank, world, local_rank):
     gf.load()
     hbm_peak, bf16_peak, peak_kind = _peaks()
 
-    batch = synth.uniform_batch(index=0)
+    batch = synth.uniform_batch(n_gens=N_GENS, index=0)
     src_h = torch.from_numpy(batch.src).pin_memory()
     coef_h = torch.from_numpy(batch.coef).pin_memory()
     src = src_h.to(dev)
@@ -512,9 +512,16 @@ def main():
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--uniform-gens", type=int, default=None,
+                    help="generations of the uniform workload (smaller cases for profiler captures; "
+                         "the reported workload is the 4096-generation batch only without it)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()
+    if args.uniform_gens is not None:
+        global N_GENS, WORKLOAD
+        N_GENS = args.uniform_gens
+        WORKLOAD = WORKLOAD.replace("4096 generations", f"{N_GENS} generations")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -266,28 +266,47 @@ __device__ __forceinline__ void load_direct(const EncGen &g, int ibase, unsigned
     }
 }
 
+// One producer lane's share of staging: the lane copies 4 bytes of rows
+// lane/8 + 4j (j = 0..7) of its warp's 32 sources, at byte positions
+// 4*(lane%8) .. +3 of its lane quarter's 32-position slice.
+struct StageLane {
+    const uint8_t *p;      // row lane/8 at column tile 0
+    const uint8_t *safe;   // any valid address (zero-size copies)
+    long long stride4;     // 4 rows
+    long long col0;        // first byte position of the lane at column tile 0
+    long long len;
+    int nrows;             // rows j with a source behind them
+    uint32_t soff;         // the lane's offset inside a stage
+};
+
+__device__ __forceinline__ StageLane stage_lane(const EncGen &g, int ibase, int quarter, int lane)
+{
+    StageLane s;
+    const int r0 = ibase + (lane >> 3);
+    s.len = (long long)g.len;
+    s.col0 = quarter * 32 + 4 * (lane & 7);
+    s.p = g.src + (size_t)r0 * g.len + s.col0;
+    s.safe = g.src;
+    s.stride4 = 4 * s.len;
+    s.nrows = g.n_src > r0 ? min(8, (g.n_src - r0 + 3) >> 2) : 0;
+    s.soff = (uint32_t)((lane >> 3) * 32 + 4 * (lane & 7));
+    return s;
+}
+
 // Stage this warp's 32 sources x 32 byte positions of column tile `ct` into
 // shared memory with 4-byte cp.async (rows 4-byte aligned); bytes outside
 // the generation are zero-filled.
-__device__ __forceinline__ void stage_tile(const EncGen &g, int ibase, int quarter, int ct, unsigned char *stage,
-                                           int lane)
+__device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned char *stage)
 {
-    const unsigned long long len = g.len;
-    const unsigned long long c0 = (unsigned long long)ct * kColTile + quarter * 32;
+    const long long rem = s.len - ((long long)ct * kColTile + s.col0);
+    const uint32_t bytes = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
+    const uint8_t *q = s.p + (long long)ct * kColTile;
+    const uint32_t dst = smem_u32(stage) + s.soff;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const int w = lane + 32 * j;      // word of the 32 x 32-byte block
-        const int row = w >> 3, wc = w & 7;
-        const int i = ibase + row;
-        const unsigned long long col = c0 + 4 * wc;
-        uint32_t bytes = 0;
-        const uint8_t *src = g.src;
-        if (i < g.n_src && col < len) {
-            bytes = (uint32_t)min(4ull, len - col);
-            src = g.src + (size_t)i * len + col;
-        }
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(stage + row * 32 + 4 * wc)),
-                     "l"(src), "r"(bytes)
+        const bool live = j < s.nrows && bytes != 0u;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 128 * j),
+                     "l"(live ? q + j * s.stride4 : s.safe), "r"(live ? bytes : 0u)
                      : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -471,10 +490,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item < 0) break;
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
+            const StageLane sl = stage_lane(g, ibase, quarter, lane);
             if (staged) {
                 // always kStages-1 groups in flight before the loop (empty ones past the row end)
                 for (int p = 0; p < kStages - 1; ++p) {
-                    if (p < ncols) stage_tile(g, ibase, quarter, p, stage + p * kStageBytes, lane);
+                    if (p < ncols) stage_tile(sl, p, stage + p * kStageBytes);
                     else asm volatile("cp.async.commit_group;" ::: "memory");
                 }
             }
@@ -483,8 +503,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 if (staged) {
                     __syncwarp();  // every lane is done reading the stage about to be refilled
                     if (ct + kStages - 1 < ncols)
-                        stage_tile(g, ibase, quarter, ct + kStages - 1, stage + ((ct + kStages - 1) % kStages) * kStageBytes,
-                                   lane);
+                        stage_tile(sl, ct + kStages - 1, stage + ((ct + kStages - 1) % kStages) * kStageBytes);
                     else
                         asm volatile("cp.async.commit_group;" ::: "memory");
                     asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
@@ -543,9 +562,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int K = g.n_coded;
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
+            const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
+            uint8_t *obase = g.out + (size_t)max(k0, 0) * len + pos;
             bool ok = true;
             for (int ct = 0; ct < ncols; ++ct) {
                 if (!mbar_wait_warp(&ctl->d_full, tiles & 1u, abort_flag)) {
@@ -568,12 +588,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     outb[t] = parity_byte(va + 4 * t);
                     outb[4 + t] = parity_byte(vb + 4 * t);
                 }
-                const unsigned long long col = (unsigned long long)ct * kColTile + pos;
-                if (col < len) {
-                    uint8_t *o = g.out + (size_t)k0 * len + col;
+                if ((unsigned long long)ct * kColTile + pos < len) {
+                    uint8_t *o = obase + (size_t)ct * kColTile;
 #pragma unroll
-                    for (int kp = 0; kp < 8; ++kp)
-                        if (k0 + kp < K) o[(size_t)kp * len] = (uint8_t)outb[kp];
+                    for (int kp = 0; kp < 8; ++kp) {
+                        if (kp < nk) *o = (uint8_t)outb[kp];
+                        o += len;
+                    }
                 }
                 ++tiles;
             }
