@@ -18,18 +18,21 @@
 //     warps straight into tensor memory with tcgen05.st (one TMEM lane per
 //     byte position, one column = the 8 bit values of one source byte);
 //   B (K = 8N x N = 256 output bits of 32 coded packets): the coefficients'
-//     bit matrices, K-major, 128-byte swizzled, double-buffered in shared
-//     memory (N <= 64: 64 KB each), built from an 8 KB per-CTA table of the
-//     256 possible 8x8 blocks;
+//     bit matrices, K-major, 128-byte swizzled, two halves of 64 KB in shared
+//     memory (N <= 64; coded packets 0..31 and 32..63 of the item), built
+//     from an 8 KB per-CTA table of the 256 possible 8x8 blocks;
 //   D (128 lanes x 256 FP32 columns): one N = 256 MMA stream per tile.  The
 //     first MMA of a tile is a rank-1 product with block scale 2^23 that sets
 //     every element to 2^23; the sum then sits in the low mantissa bits
 //     (exact: ulp(2^23) = 1), so the epilogue reads only the low 16 bits of
 //     each column (tcgen05.ld .pack::16b, two columns per register), takes
 //     bit 0 of each of the 8 values of a coded byte and packs them.
-// Work item = (generation, 32 coded packets); the CTA loops over all column
-// tiles of the item.  Roles, all running concurrently: 4 warps publish the
-// next item in a two-entry ring and build its B; 8 producer warps stage
+// Work item = (generation, up to 64 coded packets); the CTA loops over all
+// column tiles of the item, and each A tile feeds one D pass per half (so the
+// source bit planes are built once per 64 coded packets).  Roles, all running
+// concurrently: 4 warps publish the next item in a two-entry ring and build
+// each half of its B as soon as the previous item's last pass over that half
+// is done; 8 producer warps stage
 // their source rows in shared memory with cp.async two tiles ahead and fill
 // A (double-buffered in TMEM, via a 1 KB table of pre-spread words);
 // 1 thread issues the MMAs; 16 epilogue warps drain D.  Every handshake
@@ -56,7 +59,8 @@ constexpr int kMmaWarp = kProducerWarps + kEpilogueWarps;  // warp 24
 constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
 constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
-constexpr int kCodedPerItem = 32;   // coded packets per work item (MMA N = 256 output bits)
+constexpr int kCodedPerItem = 64;   // coded packets per work item: two halves
+constexpr int kCodedPerHalf = 32;   // coded packets per D pass (MMA N = 256 output bits)
 constexpr int kMaxSrc = 64;         // N limit of this path (A: 64 TMEM columns, B: 64 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
@@ -78,7 +82,7 @@ constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
 constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
-constexpr int kBBytes = 2 * kKBlock;        // 64 KB: B of one item (K <= 512)
+constexpr int kBBytes = 2 * kKBlock;        // 64 KB: B of one half item (K <= 512)
 constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
 constexpr int kTabBytes = 256 * 8 * 4;      // 8 KB: 8x8 E2M1 block of every coefficient
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
@@ -150,6 +154,21 @@ __device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, uint32_t
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();  // lane 0's acquire of the barrier phase covers the whole warp
     return ok != 0;
+}
+
+// named barrier over `count` threads that also ORs a predicate across them
+__device__ __forceinline__ bool bar_or(int id, int count, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -407,7 +426,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int bt = tid - kBWarp0 * 32;
         const int m = bt & 7;            // 16-byte chunk of a K-block: sources 4m .. 4m+3
         const int kb = (bt >> 3) & 1;    // K-block: sources 32kb .. 32kb+31
-        const int kq = bt >> 4;          // coded packets 4kq .. 4kq+3 of the item
+        const int kq = bt >> 4;          // coded packets 4kq .. 4kq+3 of a half
+        uint32_t bfills0 = 0, bfills1 = 0;  // fills of each B half so far
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (bt == 0) {
@@ -427,47 +447,56 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const long long item = ring[e];
             if (item == kSentinel) break;
             const EncGen g = ctl->ring_gen[e];
-            const int kbase = ctl->ring_k0[e];
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
             const int nkb = (N + 31) / 32;
             const int i0 = 32 * kb + 4 * m;
-            uint32_t cc[4];  // coefficients c[k][i0 .. i0+3], one byte each
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = kbase + kq * 4 + t;
-                uint32_t w = 0;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (kb < nkb && k < K && i0 + u < N) w |= (uint32_t)__ldg(g.coef + (size_t)k * ld + i0 + u) << (8 * u);
-                cc[t] = w;
-            }
-            // wait until the MMAs of the item two back are done with this buffer
-            unsigned char *Bb = Bs + e * kBBytes;
-            bool ok = true;
-            if (bt == 0) ok = mbar_wait(&ctl->b_empty[e], (use & 1u) ^ 1u, abort_flag);
-            if (bt == 0 && !ok) ctl->abort = 1;
-            asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
-            if (kb < nkb) {
+            const int nh = (min(kCodedPerItem, K - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
+            bool stop = false;
+            for (int h = 0; h < nh; ++h) {
+                const int kbase = ctl->ring_k0[e] + h * kCodedPerHalf;
+                uint32_t cc[4];  // coefficients c[k][i0 .. i0+3], one byte each
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int kp = kq * 4 + t;
-                    const uint32_t w = cc[t];
+                    const int k = kbase + kq * 4 + t;
+                    uint32_t w = 0;
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const uint32_t *tr = tab + r * 256;
-                        uint4 q;
-                        q.x = tr[w & 0xFFu];
-                        q.y = tr[(w >> 8) & 0xFFu];
-                        q.z = tr[(w >> 16) & 0xFFu];
-                        q.w = tr[w >> 24];
-                        *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, kb, m)) = q;
+                    for (int u = 0; u < 4; ++u)
+                        if (kb < nkb && k < K && i0 + u < N)
+                            w |= (uint32_t)__ldg(g.coef + (size_t)k * ld + i0 + u) << (8 * u);
+                    cc[t] = w;
+                }
+                // wait until the MMAs of the previous item are done with this half
+                unsigned char *Bb = Bs + h * kBBytes;
+                if (bt == 0 && !mbar_wait(&ctl->b_empty[h], ((h ? bfills1 : bfills0) & 1u) ^ 1u, abort_flag))
+                    ctl->abort = 1;
+                asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
+                if (kb < nkb) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int kp = kq * 4 + t;
+                        const uint32_t w = cc[t];
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const uint32_t *tr = tab + r * 256;
+                            uint4 q;
+                            q.x = tr[w & 0xFFu];
+                            q.y = tr[(w >> 8) & 0xFFu];
+                            q.z = tr[(w >> 16) & 0xFFu];
+                            q.w = tr[w >> 24];
+                            *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, kb, m)) = q;
+                        }
                     }
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // one decision for all builder threads (a per-thread read of the flag could
+                // split them across the next named barrier)
+                stop = bar_or(1, kBWarps * 32, *abort_flag != 0);
+                if (bt == 0) mbar_arrive(&ctl->b_full[h]);
+                if (h) ++bfills1;
+                else ++bfills0;
+                if (stop) break;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
-            if (bt == 0) mbar_arrive(&ctl->b_full[e]);
-            if (*abort_flag) break;
+            if (stop) break;
         }
     } else if (warp < kProducerWarps) {
         // ---------------- producers: A = source bit planes -> TMEM ----------------
@@ -558,16 +587,18 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             }
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
-            const int k0 = ctl->ring_k0[e] + oct * 8;
+            const int k0i = ctl->ring_k0[e];
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
-            const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
-            uint8_t *obase = g.out + (size_t)max(k0, 0) * len + pos;
+            const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
             bool ok = true;
-            for (int ct = 0; ct < ncols; ++ct) {
+            for (int pass = 0; pass < ncols * nh; ++pass) {
+                const int ct = nh == 2 ? pass >> 1 : pass, h = nh == 2 ? pass & 1 : 0;
+                const int k0 = k0i + h * kCodedPerHalf + oct * 8;
+                const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
                 if (!mbar_wait_warp(&ctl->d_full, tiles & 1u, abort_flag)) {
                     ctl->abort = 1;
                     ok = false;
@@ -588,8 +619,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     outb[t] = parity_byte(va + 4 * t);
                     outb[4 + t] = parity_byte(vb + 4 * t);
                 }
-                if ((unsigned long long)ct * kColTile + pos < len) {
-                    uint8_t *o = obase + (size_t)ct * kColTile;
+                if ((unsigned long long)ct * kColTile + pos < len && nk > 0) {
+                    uint8_t *o = g.out + (size_t)k0 * len + (size_t)ct * kColTile + pos;
 #pragma unroll
                     for (int kp = 0; kp < 8; ++kp) {
                         if (kp < nk) *o = (uint8_t)outb[kp];
@@ -603,6 +634,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     } else if (lane == 0) {
         // ---------------- MMA issuer (warp kMmaWarp, one thread) ----------------
         uint32_t fills = 0, tiles = 0;
+        uint32_t bused0 = 0, bused1 = 0;  // fills of each B half consumed so far
         const uint64_t bias_desc = b_desc(smem_u32(bias_b));
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
@@ -616,37 +648,49 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item < 0) break;
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const int ksteps = (g.n_src + 7) / 8;  // 8 sources = 64 E2M1 values per MMA
-            bool ok = mbar_wait(&ctl->b_full[e], use & 1u, abort_flag);
-            tc_fence_after();
-            const uint64_t bdesc0 = b_desc(smem_u32(Bs + e * kBBytes));
+            const int nh = (min(kCodedPerItem, g.n_coded - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
+            bool ok = true;
             for (int ct = 0; ct < ncols && ok; ++ct) {
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
                 if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
-                if (!mbar_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
-                // B lies below 256 KB of shared memory)
-                const uint32_t dt = tmem + kDCol0;
                 const uint32_t at = tmem + buf * kABufCols;
-                tc_mma(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
+                // the A tile serves both halves of the item: one D pass per 32 coded packets
+                for (int h = 0; h < nh; ++h) {
+                    if (ct == 0 && !mbar_wait(&ctl->b_full[h], (h ? bused1 : bused0) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
+                    // B lies below 256 KB of shared memory)
+                    const uint64_t bdesc0 = b_desc(smem_u32(Bs + h * kBBytes));
+                    const uint32_t dt = tmem + kDCol0;
+                    tc_mma(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    if (s < ksteps)
-                        tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
-                               tmem + kSfOneA, tmem + kSfOneB, 1u);
+                    for (int s = 0; s < 8; ++s) {
+                        if (s < ksteps)
+                            tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4),
+                                   kIdesc, tmem + kSfOneA, tmem + kSfOneB, 1u);
+                    }
+                    tc_commit(&ctl->d_full);
+                    if (ct == ncols - 1) {
+                        tc_commit(&ctl->b_empty[h]);  // this half of B is free for the next item
+                        if (h) ++bused1;
+                        else ++bused0;
+                    }
+                    ++tiles;
                 }
-                tc_commit(&ctl->d_full);
+                if (!ok) break;
                 tc_commit(&ctl->a_empty[buf]);
                 ++fills;
-                ++tiles;
             }
-            tc_commit(&ctl->b_empty[e]);
             if (!ok) {
                 ctl->abort = 1;
                 break;
