@@ -145,17 +145,6 @@ __device__ __noinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
     }
 }
 
-// Warp-uniform bounded wait: lane 0 waits, the warp adopts its outcome, so
-// the warp-collective tcgen05.ld/st that follow always run with all lanes.
-__device__ __forceinline__ bool mbar_wait_warp(unsigned long long *bar, uint32_t parity, volatile int *abort)
-{
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();  // lane 0's acquire of the barrier phase covers the whole warp
-    return ok != 0;
-}
-
 // named barrier over `count` threads that also ORs a predicate across them
 __device__ __forceinline__ bool bar_or(int id, int count, bool pred)
 {
@@ -169,6 +158,17 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool pred)
         : "r"((uint32_t)pred), "r"(id), "r"(count)
         : "memory");
     return r != 0;
+}
+
+// Wait of a whole role: one thread polls the mbarrier (bounded), the role's
+// other warps block on named barrier `id` (no issue slots while blocked) and
+// all of them adopt the outcome.  Returns false if the wait gave up.
+__device__ __forceinline__ bool role_wait(unsigned long long *bar, uint32_t parity, volatile int *abort, bool poller,
+                                          int id, int count)
+{
+    bool fail = false;
+    if (poller) fail = !mbar_wait(bar, parity, abort);
+    return !bar_or(id, count, fail);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -505,10 +505,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int pos = quarter * 32 + lane;   // byte position within the column tile
         const int ibase = part * kSrcPerProducer;
         unsigned char *stage = staging + warp * (kStages * kStageBytes);
+        const bool poller = tid == 0;
         uint32_t fills = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
-            if (!mbar_wait_warp(&ctl->info_full[e], use & 1u, abort_flag)) {
+            if (!role_wait(&ctl->info_full[e], use & 1u, abort_flag, poller, 3, kProducerWarps * 32)) {
                 ctl->abort = 1;
                 break;
             }
@@ -539,7 +540,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     __syncwarp();
                 }
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
-                if (!mbar_wait_warp(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag)) {
+                if (!role_wait(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag, poller, 3, kProducerWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;
                     break;
@@ -578,10 +579,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int quarter = warp & 3;
         const int oct = (warp - kProducerWarps) >> 2;   // 8-packet group of the item: 0..3
         const int pos = quarter * 32 + lane;
+        const bool poller = tid == kProducerWarps * 32;
         uint32_t tiles = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
-            if (!mbar_wait_warp(&ctl->info_full[e], use & 1u, abort_flag)) {
+            if (!role_wait(&ctl->info_full[e], use & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                 ctl->abort = 1;
                 break;
             }
@@ -599,7 +601,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 const int ct = nh == 2 ? pass >> 1 : pass, h = nh == 2 ? pass & 1 : 0;
                 const int k0 = k0i + h * kCodedPerHalf + oct * 8;
                 const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
-                if (!mbar_wait_warp(&ctl->d_full, tiles & 1u, abort_flag)) {
+                if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;
                     break;
