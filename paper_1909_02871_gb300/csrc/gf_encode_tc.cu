@@ -258,7 +258,7 @@ __device__ __forceinline__ uint32_t parity_byte(const uint32_t *v)
 {
     const uint32_t q0 = prmt(v[0], v[1], 0x6420u) & 0x01010101u;
     const uint32_t q1 = prmt(v[2], v[3], 0x6420u) & 0x01010101u;
-    return ((q0 * 0x01020408u) >> 24) | (((q1 * 0x01020408u) >> 24) << 4);
+    return ((q1 * 16u + q0) * 0x01020408u) >> 24;
 }
 
 __device__ __forceinline__ int locate(const long long *tile_start, int n_gens, long long item)
