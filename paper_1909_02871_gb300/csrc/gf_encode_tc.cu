@@ -253,7 +253,11 @@ __host__ __device__ __forceinline__ uint32_t spread_bits(uint32_t b)
 }
 
 // parity byte of 8 biased sums, low 16 bits packed two per word (word j =
-// output bits 2j, 2j+1): bit 0 of each half is the parity of that sum
+// output bits 2j, 2j+1): bit 0 of each half is the parity of that sum.  The
+// low bytes of the halves are gathered (bits 0..3 into q0, 4..7 into q1),
+// q1's bytes moved up by 4, and one multiply collects bit 0 of byte j at
+// bit 24 + j and bit 4 of byte j at bit 28 + j (no carries reach bits
+// 24..31 from the other partial products).
 __device__ __forceinline__ uint32_t parity_byte(const uint32_t *v)
 {
     const uint32_t q0 = prmt(v[0], v[1], 0x6420u) & 0x01010101u;
