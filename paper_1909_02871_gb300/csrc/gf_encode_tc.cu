@@ -32,14 +32,15 @@
 // source bit planes are built once per 64 coded packets).  Roles, all running
 // concurrently: 4 warps publish the next item in a two-entry ring and build
 // each half of its B as soon as the previous item's last pass over that half
-// is done; 8 producer warps stage
-// their source rows in shared memory with cp.async two tiles ahead and fill
-// A (double-buffered in TMEM, via a 1 KB table of pre-spread words);
-// 1 thread issues the MMAs; 16 epilogue warps drain D.  Every handshake
-// arrives once per warp (after __syncwarp), never once per thread.  Every
-// mbarrier wait is bounded by the global timer; a wait that gives up
-// records GF_ETIMEOUT in the library's device status word, the CTA drains
-// its MMAs (bounded), frees TMEM and exits.
+// is done; 8 producer warps stage their source rows in shared memory with
+// cp.async two tiles ahead and fill A (double-buffered in TMEM, via a 1 KB
+// table of pre-spread words); 1 thread issues the MMAs; 16 epilogue warps
+// drain D.  Handshakes arrive once per warp (after __syncwarp).  A role of
+// several warps waits through one elected thread that polls the mbarrier
+// while the others are parked on a named barrier, which also hands every
+// warp the same outcome.  Every mbarrier wait is bounded by the global
+// timer; a wait that gives up records GF_ETIMEOUT in the library's device
+// status word, the CTA drains its MMAs (bounded), frees TMEM and exits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
