@@ -245,9 +245,11 @@ static long long table_tiles(EncGen &g)
 void finalize_batch(EncodeBatch &b)
 {
     b.tile_start.assign(b.gens.size() + 1, 0);
+    b.all_gf256 = true;
     long long t = 0;
     for (size_t i = 0; i < b.gens.size(); ++i) {
         b.tile_start[i] = t;
+        if (b.gens[i].field != 8) b.all_gf256 = false;
         long long n;
         if (b.kind == GF_PATH_BITSLICED) n = bitsliced_tiles(b.gens[i], b.gens[i].col_chunks, b.gens[i].k_chunks);
         else n = table_tiles(b.gens[i]);
@@ -331,7 +333,7 @@ int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBa
         int p = path;
         if (p == GF_PATH_AUTO) p = choose_path(g.field, g.n_src, g.n_coded, g.len);
         if (p == GF_PATH_BITSLICED) {
-            if (g.field != 8 || !bitsliced_available()) {
+            if (!bitsliced_available()) {
                 if (path == GF_PATH_BITSLICED) return GF_ENOTSUP;
                 p = GF_PATH_TABLE;
             } else if (!bitsliced_supports(g)) {

@@ -38,6 +38,7 @@ struct EncodeBatch {
     std::vector<EncGen> gens;
     std::vector<long long> tile_start;  // n_gens + 1 prefix sums
     long long total_tiles = 0;
+    bool all_gf256 = true;  // bit-sliced: every generation is GF(256) (specialised kernel)
     // device copies (inside a workspace or plan buffer)
     WorkCounter *d_counter = nullptr;
     EncGen *d_gens = nullptr;

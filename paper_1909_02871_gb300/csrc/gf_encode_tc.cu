@@ -85,7 +85,12 @@ constexpr long long kSentinel = -1;
 constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
 constexpr int kBBytes = 2 * kKBlock;        // 64 KB: B of one half item (K <= 512)
 constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
-constexpr int kTabBytes = 256 * 8 * 4;      // 8 KB: 8x8 E2M1 block of every coefficient
+// 8x8 E2M1 blocks of every coefficient of GF(256), GF(16), GF(4), GF(2):
+// row r of the block of c in field GF(2^n) is word r * 256 + base(n) + c,
+// GF(256) in rows 0..7, the small fields side by side in rows 8..15
+constexpr int kTabBase8 = 0, kTabBase4 = 8 * 256, kTabBase2 = 8 * 256 + 16, kTabBase1 = 8 * 256 + 16 + 4;
+constexpr int kTabRow = 256;
+constexpr int kTabBytes = 16 * 1024;
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
 constexpr int kSpreadBytes = 256 * 4;       // 1 KB: the 8 E2M1 bit values of every source byte
 constexpr int kSmemBytes =
@@ -343,6 +348,9 @@ __device__ __forceinline__ uint32_t b_chunk(int n, int kb, int m)
     return (uint32_t)(kb * kKBlock + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
 }
 
+// kAnyField = false: every generation of the launch is GF(256) (only that
+// table is built and the B builder indexes it directly); true: any field.
+template <bool kAnyField>
 __global__ void __launch_bounds__(kThreads, 1)
 encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__restrict__ tile_start, int n_gens,
                         long long total, WorkCounter *ctr, int *status)
@@ -351,7 +359,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Bs = smem;                                // two B buffers
     unsigned char *bias_b = smem + 2 * kBBytes;
-    uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][c]
+    uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][field][c]
     unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
     uint32_t *spread = reinterpret_cast<uint32_t *>(staging + kStageAll);  // [source byte]
     Ctl *ctl = reinterpret_cast<Ctl *>(reinterpret_cast<unsigned char *>(spread) + kSpreadBytes);
@@ -360,10 +368,14 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // the 8x8 E2M1 block of every coefficient: row r, nibble j = bit r of
-    // c*x^j, stored [r][c] so that lanes looking up different coefficients
-    // for the same row spread over all shared-memory banks
-    for (int e = tid; e < 256 * 8; e += blockDim.x) {
+    // The 8x8 E2M1 block of every coefficient of every field.  A byte holds
+    // 8/n words of GF(2^n) (word w in bits [wn, wn+n)), all multiplied by
+    // the same c, so the block is block-diagonal: output bit r (word r/n,
+    // bit r%n), input bit j (word j/n, bit j%n) is bit r%n of c*x^(j%n)
+    // when both lie in the same word.  Row r is one word, nibble j = that
+    // bit; tables are [r][c] so that lanes looking up different
+    // coefficients for the same row spread over the shared-memory banks.
+    for (int e = tid; e < 8 * 256; e += blockDim.x) {
         const uint32_t c = (uint32_t)e & 255u, r = (uint32_t)e >> 8;
         uint32_t p = c, row = 0;
         for (int j = 0; j < 8; ++j) {
@@ -371,6 +383,20 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             p = xtime(8, p);
         }
         tab[e] = row;
+    }
+    if (kAnyField) {
+        for (int e = tid; e < 8 * 22; e += blockDim.x) {
+            const int r = e / 22, col = e % 22;
+            const int lg = col < 16 ? 2 : col < 20 ? 1 : 0;  // n = 2^lg
+            const int n = 1 << lg;
+            const uint32_t c = (uint32_t)(lg == 2 ? col : lg == 1 ? col - 16 : col - 20);
+            uint32_t row = 0, p = c;
+            for (int j = 0; j < 8; ++j) {
+                p = (j & (n - 1)) == 0 ? c : xtime(n, p);  // c * x^(j % n)
+                if ((r >> lg) == (j >> lg) && ((p >> (r & (n - 1))) & 1u)) row |= kOne << (4 * j);
+            }
+            tab[kTabBase4 + r * kTabRow + col] = row;
+        }
     }
     for (int v = tid; v < 256; v += blockDim.x) spread[v] = spread_bits((uint32_t)v);
     // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
@@ -454,6 +480,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const EncGen g = ctl->ring_gen[e];
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
             const int nkb = (N + 31) / 32;
+            const uint32_t *ftab =
+                kAnyField ? tab + (g.field == 8 ? kTabBase8 : g.field == 4 ? kTabBase4 : g.field == 2 ? kTabBase2 : kTabBase1)
+                          : tab;
             const int i0 = 32 * kb + 4 * m;
             const int nh = (min(kCodedPerItem, K - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
             bool stop = false;
@@ -482,7 +511,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                         const uint32_t w = cc[t];
 #pragma unroll
                         for (int r = 0; r < 8; ++r) {
-                            const uint32_t *tr = tab + r * 256;
+                            const uint32_t *tr = ftab + r * kTabRow;
                             uint4 q;
                             q.x = tr[w & 0xFFu];
                             q.y = tr[(w >> 8) & 0xFFu];
@@ -753,7 +782,7 @@ bool bitsliced_available()
 
 bool bitsliced_supports(const EncGen &g)
 {
-    return g.field == 8 && g.n_src > 0 && g.n_src <= tc::kMaxSrc && g.n_coded > 0 && g.len > 0;
+    return (g.field == 1 || g.field == 2 || g.field == 4 || g.field == 8) && g.n_src > 0 && g.n_src <= tc::kMaxSrc && g.n_coded > 0 && g.len > 0;
 }
 
 long long bitsliced_tiles(const EncGen &g, int &col_chunks, int &k_chunks)
@@ -775,7 +804,9 @@ int launch_bitsliced(const EncodeBatch &b, cudaStream_t stream)
         std::lock_guard<std::mutex> lock(mu);
         const int dev = current_device();
         if (dev != configured_dev) {
-            if (cudaFuncSetAttribute(tc::encode_bitsliced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (cudaFuncSetAttribute(tc::encode_bitsliced_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::kSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(tc::encode_bitsliced_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      tc::kSmemBytes) != cudaSuccess)
                 return GF_ECUDA;
             configured_dev = dev;
@@ -784,8 +815,12 @@ int launch_bitsliced(const EncodeBatch &b, cudaStream_t stream)
     int *status = device_status_word();
     if (!status) return GF_ENOMEM;
     const long long grid = std::min<long long>(b.total_tiles, sm_count());
-    tc::encode_bitsliced_kernel<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(
-        b.d_gens, b.d_tile_start, (int)b.gens.size(), b.total_tiles, b.d_counter, status);
+    if (b.all_gf256)
+        tc::encode_bitsliced_kernel<false><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(
+            b.d_gens, b.d_tile_start, (int)b.gens.size(), b.total_tiles, b.d_counter, status);
+    else
+        tc::encode_bitsliced_kernel<true><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(
+            b.d_gens, b.d_tile_start, (int)b.gens.size(), b.total_tiles, b.d_counter, status);
     return cuda_status(cudaGetLastError());
 }
 

@@ -82,11 +82,33 @@ def _bitsliced_ok():
         raise
 
 
-def test_bitsliced_rejects_other_fields():
-    src = np.zeros((4, 64), np.uint8)
-    coef = np.ones((4, 4), np.uint8)
-    s, c, o = to_dev(src.reshape(-1)), to_dev(coef.reshape(-1)), torch.zeros(256, dtype=torch.uint8, device=dev())
-    assert gf.encode_status([(4, 4, 4, 64, s, c, o)], path=gf.PATH_BITSLICED) == gf.GF_ENOTSUP
+@pytest.mark.parametrize("field", FIELDS)
+@pytest.mark.parametrize("shape", [(64, 64, 1500), (17, 40, 777), (1, 1, 1), (64, 33, 129), (40, 64, 4096)])
+def test_bitsliced_every_field(field, shape):
+    """GF(2), GF(4), GF(16) bytes hold 8/n words multiplied by the same
+    coefficient: the bit-sliced path uses block-diagonal 8x8 matrices."""
+    if not _bitsliced_ok():
+        pytest.skip("bit-sliced path unavailable")
+    N, K, L = shape
+    g = synth.choice(61, field, N, K, L)
+    src = synth.random_bytes(g, (N, L))
+    coef = synth.coefficients(g, field, (K, N), nonzero=False)
+    (out,) = _run([(field, src, coef)], path=gf.PATH_BITSLICED)
+    assert np.array_equal(out, oracle.encode(field, src, coef))
+
+
+def test_bitsliced_mixed_fields_one_launch():
+    if not _bitsliced_ok():
+        pytest.skip("bit-sliced path unavailable")
+    g = synth.choice(62)
+    items = []
+    for i in range(24):
+        field = FIELDS[i % 4]
+        N, K, L = int(g.integers(1, 65)), int(g.integers(1, 100)), int(g.integers(1, 3000))
+        items.append((field, synth.random_bytes(g, (N, L)), synth.coefficients(g, field, (K, N), nonzero=False)))
+    outs = _run(items, path=gf.PATH_BITSLICED)
+    for (field, src, coef), out in zip(items, outs):
+        assert np.array_equal(out, oracle.encode(field, src, coef)), (field, src.shape, coef.shape)
 
 
 @pytest.mark.parametrize("shape", [(64, 64, 1500), (16, 16, 1500), (1, 1, 1), (33, 70, 255), (128, 96, 4097),
