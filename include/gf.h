@@ -111,7 +111,7 @@ typedef struct gf_gen {
 /* Encode paths. */
 #define GF_PATH_AUTO 0       /* autotuned choice per shape bucket */
 #define GF_PATH_TABLE 1      /* per-coefficient split tables, prmt lookups, integer ALU */
-#define GF_PATH_BITSLICED 2  /* 8x8 GF(2) bit matrices on the tensor cores (E2M1), any field, N <= 64 */
+#define GF_PATH_BITSLICED 2  /* 8x8 GF(2) bit matrices on the tensor cores (E2M1), any field */
 
 /*
  * gf_encode_batched: encode n_gens generations (uneven N, K, len and field
@@ -124,8 +124,7 @@ typedef struct gf_gen {
 int gf_encode_batched(const gf_gen_t *gens, int n_gens, gf_stream_t stream);
 
 /* As gf_encode_batched with an explicit path (GF_PATH_*).  GF_PATH_BITSLICED
- * returns GF_ENOTSUP on a device without sm_103 tensor cores; generations it
- * does not cover (N > 64) run on the table path within the same call. */
+ * returns GF_ENOTSUP on a device without sm_103 tensor cores. */
 int gf_encode_batched_ex(const gf_gen_t *gens, int n_gens, int path, gf_stream_t stream);
 
 /*

@@ -355,6 +355,15 @@ int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBa
         out.push_back(std::move(table));
     }
     if (!bits.gens.empty()) {
+        // the persistent CTAs take work items in order: the longest items
+        // (64-source chunks x column tiles x 32-packet halves) go first so
+        // that no long item starts near the end
+        auto item_cost = [](const EncGen &g) {
+            return (long long)((g.n_src + 63) / 64) * (long long)((g.len + 127) / 128) *
+                   (long long)std::min(2, (g.n_coded + 31) / 32);
+        };
+        std::stable_sort(bits.gens.begin(), bits.gens.end(),
+                         [&](const EncGen &a, const EncGen &b) { return item_cost(a) > item_cost(b); });
         finalize_batch(bits);
         out.push_back(std::move(bits));
     }

@@ -1,6 +1,6 @@
-// gf_encode_tc.cu -- bit-sliced GF(256) generation encode on the sm_103a
-// tensor cores (tcgen05 kind::mxf4 block-scaled MMA, FP32 accumulators in
-// TMEM).
+// gf_encode_tc.cu -- bit-sliced generation encode (GF(2), GF(4), GF(16),
+// GF(256)) on the sm_103a tensor cores (tcgen05 kind::mxf4 block-scaled MMA,
+// FP32 accumulators in TMEM).
 //
 // The imul algorithm of section IV-B rests on the identity
 //     c * a = XOR_j a_j * (c * x^j),        a_j = bit j of a,
@@ -9,7 +9,9 @@
 // binary matrix product:
 //     bit r of out_k[l] = sum_{i,j} bit_j(src_i[l]) * bit_r(c_ki * x^j)  (mod 2)
 // The tensor core computes the integer sum exactly (0/1 operands, at most
-// 512 terms) and the parity is the result's lowest bit.  The operands are
+// 512 terms per 64-source chunk) and the parity is the result's lowest bit;
+// the parities of the chunks of a larger generation are XORed together
+// (Eq. 2 is a sum over sources).  The operands are
 // E2M1 (4-bit) values 0 and 1.0 with every block scale 1.0 (UE8M0 127),
 // which runs at twice the FP8 rate.  The kernel computes the product
 // transposed, one 128-byte column tile at a time:
@@ -19,17 +21,19 @@
 //     byte position, one column = the 8 bit values of one source byte);
 //   B (K = 8N x N = 256 output bits of 32 coded packets): the coefficients'
 //     bit matrices, K-major, 128-byte swizzled, two halves of 64 KB in shared
-//     memory (N <= 64; coded packets 0..31 and 32..63 of the item), built
-//     from an 8 KB per-CTA table of the 256 possible 8x8 blocks;
+//     memory (64 sources; coded packets 0..31 and 32..63 of the item), built
+//     from a per-CTA table of the 8x8 blocks of every coefficient;
 //   D (128 lanes x 256 FP32 columns): one N = 256 MMA stream per tile.  The
 //     first MMA of a tile is a rank-1 product with block scale 2^23 that sets
 //     every element to 2^23; the sum then sits in the low mantissa bits
 //     (exact: ulp(2^23) = 1), so the epilogue reads only the low 16 bits of
 //     each column (tcgen05.ld .pack::16b, two columns per register), takes
 //     bit 0 of each of the 8 values of a coded byte and packs them.
-// Work item = (generation, up to 64 coded packets); the CTA loops over all
-// column tiles of the item, and each A tile feeds one D pass per half (so the
-// source bit planes are built once per 64 coded packets).  Roles, all running
+// Work item = (generation, up to 64 coded packets); the CTA loops over the
+// item's 64-source chunks and, within each, over all column tiles; each A
+// tile feeds one D pass per half (so the source bit planes are built once
+// per 64 coded packets).  The first chunk's passes write the coded bytes,
+// later chunks' passes XOR into them (the same thread owns the same bytes).  Roles, all running
 // concurrently: 4 warps publish the next item in a two-entry ring and build
 // each half of its B as soon as the previous item's last pass over that half
 // is done; 8 producer warps stage their source rows in shared memory with
@@ -62,7 +66,7 @@ constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerItem = 64;   // coded packets per work item: two halves
 constexpr int kCodedPerHalf = 32;   // coded packets per D pass (MMA N = 256 output bits)
-constexpr int kMaxSrc = 64;         // N limit of this path (A: 64 TMEM columns, B: 64 KB)
+constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: 64 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
 constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte positions
@@ -477,16 +481,21 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
             const long long item = ring[e];
             if (item == kSentinel) break;
-            const EncGen g = ctl->ring_gen[e];
+            const EncGen &g = ctl->ring_gen[e];  // read from shared memory where used
             const int N = g.n_src, K = g.n_coded, ld = g.coef_ld;
-            const int nkb = (N + 31) / 32;
+            const uint8_t *coef = g.coef;
+            const int nkc = (N + kMaxSrc - 1) / kMaxSrc;  // chunks of 64 sources
+            const int field = g.field;
             const uint32_t *ftab =
-                kAnyField ? tab + (g.field == 8 ? kTabBase8 : g.field == 4 ? kTabBase4 : g.field == 2 ? kTabBase2 : kTabBase1)
+                kAnyField ? tab + (field == 8 ? kTabBase8 : field == 4 ? kTabBase4 : field == 2 ? kTabBase2 : kTabBase1)
                           : tab;
-            const int i0 = 32 * kb + 4 * m;
             const int nh = (min(kCodedPerItem, K - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
             bool stop = false;
-            for (int h = 0; h < nh; ++h) {
+            // one B half per (source chunk kc, half h), in the order the MMAs consume them
+            for (int u = 0; u < nkc * nh; ++u) {
+                const int kc = nh == 2 ? u >> 1 : u, h = nh == 2 ? u & 1 : 0;
+                const int i0 = kMaxSrc * kc + 32 * kb + 4 * m;
+                const int nkb = (min(kMaxSrc, N - kMaxSrc * kc) + 31) / 32;
                 const int kbase = ctl->ring_k0[e] + h * kCodedPerHalf;
                 uint32_t cc[4];  // coefficients c[k][i0 .. i0+3], one byte each
 #pragma unroll
@@ -496,7 +505,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (kb < nkb && k < K && i0 + u < N)
-                            w |= (uint32_t)__ldg(g.coef + (size_t)k * ld + i0 + u) << (8 * u);
+                            w |= (uint32_t)__ldg(coef + (size_t)k * ld + i0 + u) << (8 * u);
                     cc[t] = w;
                 }
                 // wait until the MMAs of the previous item are done with this half
@@ -554,22 +563,33 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (item < 0) break;
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
-            const StageLane sl = stage_lane(g, ibase, quarter, lane);
+            // units = (64-source chunk, column tile), chunk-major: the order the MMAs consume A
+            const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             if (staged) {
-                // always kStages-1 groups in flight before the loop (empty ones past the row end)
+                // always kStages-1 groups in flight before the loop (empty ones past the last unit)
                 for (int p = 0; p < kStages - 1; ++p) {
-                    if (p < ncols) stage_tile(sl, p, stage + p * kStageBytes);
-                    else asm volatile("cp.async.commit_group;" ::: "memory");
+                    if (p < nunits) {
+                        const int kc = p / ncols;
+                        stage_tile(stage_lane(g, kc * kMaxSrc + ibase, quarter, lane), p - kc * ncols,
+                                   stage + p * kStageBytes);
+                    } else {
+                        asm volatile("cp.async.commit_group;" ::: "memory");
+                    }
                 }
             }
             bool ok = true;
-            for (int ct = 0; ct < ncols; ++ct) {
+            for (int v = 0; v < nunits; ++v) {
+                const int kc = v / ncols, ct = v - kc * ncols;
                 if (staged) {
                     __syncwarp();  // every lane is done reading the stage about to be refilled
-                    if (ct + kStages - 1 < ncols)
-                        stage_tile(sl, ct + kStages - 1, stage + ((ct + kStages - 1) % kStages) * kStageBytes);
-                    else
+                    const int vs = v + kStages - 1;
+                    if (vs < nunits) {
+                        const int kcs = vs / ncols;
+                        stage_tile(stage_lane(g, kcs * kMaxSrc + ibase, quarter, lane), vs - kcs * ncols,
+                                   stage + (vs % kStages) * kStageBytes);
+                    } else {
                         asm volatile("cp.async.commit_group;" ::: "memory");
+                    }
                     asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
                     __syncwarp();
                 }
@@ -581,7 +601,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 }
                 tc_fence_after();
                 const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 32;
-                const unsigned char *sb = stage + (ct % kStages) * kStageBytes + lane;
+                const unsigned char *sb = stage + (v % kStages) * kStageBytes + lane;
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     uint32_t v[16];
@@ -592,7 +612,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 #pragma unroll
                             for (int t = 0; t < 8; ++t) b[t] = sb[((2 * half + grp) * 8 + t) * 32];
                         } else {
-                            load_direct(g, ibase, (unsigned long long)ct * kColTile + pos, b, 2 * half + grp);
+                            load_direct(g, kc * kMaxSrc + ibase, (unsigned long long)ct * kColTile + pos, b,
+                                        2 * half + grp);
                         }
 #pragma unroll
                         for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread[b[t]];
@@ -630,9 +651,12 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const unsigned long long len = g.len;
             const int ncols = (int)((len + kColTile - 1) / kColTile);
             const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
+            const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             bool ok = true;
-            for (int pass = 0; pass < ncols * nh; ++pass) {
-                const int ct = nh == 2 ? pass >> 1 : pass, h = nh == 2 ? pass & 1 : 0;
+            for (int pass = 0; pass < nunits * nh; ++pass) {
+                const int v = nh == 2 ? pass >> 1 : pass, h = nh == 2 ? pass & 1 : 0;
+                const bool first = v < ncols;  // source chunk 0 writes, later chunks add (XOR) their share
+                const int ct = first ? v : v % ncols;
                 const int k0 = k0i + h * kCodedPerHalf + oct * 8;
                 const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
                 if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
@@ -657,10 +681,19 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 }
                 if ((unsigned long long)ct * kColTile + pos < len && nk > 0) {
                     uint8_t *o = g.out + (size_t)k0 * len + (size_t)ct * kColTile + pos;
+                    if (first) {
 #pragma unroll
-                    for (int kp = 0; kp < 8; ++kp) {
-                        if (kp < nk) *o = (uint8_t)outb[kp];
-                        o += len;
+                        for (int kp = 0; kp < 8; ++kp) {
+                            if (kp < nk) *o = (uint8_t)outb[kp];
+                            o += len;
+                        }
+                    } else {
+                        // this thread wrote these bytes for the earlier chunks (same lane, same packets)
+#pragma unroll
+                        for (int kp = 0; kp < 8; ++kp) {
+                            if (kp < nk) *o = (uint8_t)(*o ^ outb[kp]);
+                            o += len;
+                        }
                     }
                 }
                 ++tiles;
@@ -683,17 +716,20 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const int ncols = (int)((g.len + kColTile - 1) / kColTile);
-            const int ksteps = (g.n_src + 7) / 8;  // 8 sources = 64 E2M1 values per MMA
+            const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             const int nh = (min(kCodedPerItem, g.n_coded - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
             bool ok = true;
-            for (int ct = 0; ct < ncols && ok; ++ct) {
+            for (int v = 0; v < nunits && ok; ++v) {
+                const int kc = v / ncols, ct = v - kc * ncols;  // 64-source chunk, column tile
+                const int ksteps = (min(kMaxSrc, g.n_src - kc * kMaxSrc) + 7) / 8;  // 8 sources per MMA
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
                 if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
                 const uint32_t at = tmem + buf * kABufCols;
-                // the A tile serves both halves of the item: one D pass per 32 coded packets
+                // the A tile serves both halves of the item: one D pass per 32 coded packets (each
+                // source chunk's B halves are built anew, so they are waited for at its first tile)
                 for (int h = 0; h < nh; ++h) {
                     if (ct == 0 && !mbar_wait(&ctl->b_full[h], (h ? bused1 : bused0) & 1u, abort_flag)) {
                         ok = false;
@@ -782,7 +818,8 @@ bool bitsliced_available()
 
 bool bitsliced_supports(const EncGen &g)
 {
-    return (g.field == 1 || g.field == 2 || g.field == 4 || g.field == 8) && g.n_src > 0 && g.n_src <= tc::kMaxSrc && g.n_coded > 0 && g.len > 0;
+    return (g.field == 1 || g.field == 2 || g.field == 4 || g.field == 8) && g.n_src > 0 && g.n_coded > 0 &&
+           g.len > 0;
 }
 
 long long bitsliced_tiles(const EncGen &g, int &col_chunks, int &k_chunks)

@@ -78,7 +78,7 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len)
     }
     // GF(2) is a plain XOR of the chosen sources on the table path; the other
     // fields go to the tensor cores once the product is large enough
-    if (field != 1 && bitsliced_available() && n_src >= 32 && n_src <= 64 && n_coded >= 32 && len >= 512)
+    if (field != 1 && bitsliced_available() && n_src >= 32 && n_coded >= 32 && len >= 512)
         return GF_PATH_BITSLICED;
     return GF_PATH_TABLE;
 }
@@ -259,7 +259,7 @@ extern "C" int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t le
                            buf + src_b + (size_t)i * n_coded * n_src, buf + src_b + coef_b + (size_t)i * n_coded * len};
     }
     std::vector<TuneChoice> cands;
-    if (bitsliced_available() && n_src <= 64) cands.push_back({GF_PATH_BITSLICED, 0});
+    if (bitsliced_available()) cands.push_back({GF_PATH_BITSLICED, 0});
     for (int v = 0; v < kNumTableVariants; ++v) cands.push_back({GF_PATH_TABLE, v});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

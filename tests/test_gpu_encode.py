@@ -83,10 +83,12 @@ def _bitsliced_ok():
 
 
 @pytest.mark.parametrize("field", FIELDS)
-@pytest.mark.parametrize("shape", [(64, 64, 1500), (17, 40, 777), (1, 1, 1), (64, 33, 129), (40, 64, 4096)])
+@pytest.mark.parametrize("shape", [(64, 64, 1500), (17, 40, 777), (1, 1, 1), (64, 33, 129), (40, 64, 4096),
+                                   (65, 70, 300), (130, 64, 1000), (255, 33, 257)])
 def test_bitsliced_every_field(field, shape):
     """GF(2), GF(4), GF(16) bytes hold 8/n words multiplied by the same
-    coefficient: the bit-sliced path uses block-diagonal 8x8 matrices."""
+    coefficient: the bit-sliced path uses block-diagonal 8x8 matrices.  N > 64
+    runs in 64-source chunks whose parities are XORed together."""
     if not _bitsliced_ok():
         pytest.skip("bit-sliced path unavailable")
     N, K, L = shape
@@ -104,7 +106,7 @@ def test_bitsliced_mixed_fields_one_launch():
     items = []
     for i in range(24):
         field = FIELDS[i % 4]
-        N, K, L = int(g.integers(1, 65)), int(g.integers(1, 100)), int(g.integers(1, 3000))
+        N, K, L = int(g.integers(1, 256)), int(g.integers(1, 100)), int(g.integers(1, 3000))
         items.append((field, synth.random_bytes(g, (N, L)), synth.coefficients(g, field, (K, N), nonzero=False)))
     outs = _run(items, path=gf.PATH_BITSLICED)
     for (field, src, coef), out in zip(items, outs):
