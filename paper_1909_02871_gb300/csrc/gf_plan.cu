@@ -69,6 +69,9 @@ int choose_table_variant(int field, int n_src, int n_coded, unsigned long long l
     return n_coded <= 8 ? 3 : 0;          // 512-byte column tiles
 }
 
+constexpr int kBitslicedMinSrc = 16, kBitslicedMinCoded = 16;
+constexpr unsigned long long kBitslicedMinLen = 256;
+
 int choose_path(int field, int n_src, int n_coded, unsigned long long len)
 {
     {
@@ -76,9 +79,11 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len)
         auto it = g_tune.find(tune_key(field, n_src, n_coded, len));
         if (it != g_tune.end()) return it->second.path;
     }
-    // GF(2) is a plain XOR of the chosen sources on the table path; the other
-    // fields go to the tensor cores once the product is large enough
-    if (field != 1 && bitsliced_available() && n_src >= 32 && n_coded >= 32 && len >= 512)
+    // every field goes to the tensor cores once a 128-byte x 32-packet x
+    // 64-source pass holds enough work to beat the table path's integer
+    // operations per word and coefficient
+    if (bitsliced_available() && n_src >= kBitslicedMinSrc && n_coded >= kBitslicedMinCoded &&
+        len >= kBitslicedMinLen)
         return GF_PATH_BITSLICED;
     return GF_PATH_TABLE;
 }
