@@ -14,8 +14,9 @@
 //      drop the row if there is none, normalise it by the pivot's inverse,
 //      eliminate its pivot column from every stored row, store it.  It stops
 //      at rank N.  Row operations are split-table region madds on 32-bit
-//      words in shared memory (gf::ByteMap), the elimination of the new row
-//      sums partial products per warp and combines them with shared-memory
+//      words in shared memory (gf::ByteMap); in the elimination of the new
+//      row each warp sums the products of a share of the stored rows in
+//      registers and the warps' sums are combined with shared-memory
 //      atomicXor.  Output: X (N x R), where row p of X expresses decoded
 //      source p in the received rows (zero if p is not determined), plus
 //      rank, rows consumed and per-source flags.
@@ -48,11 +49,34 @@ size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem)
     size_t b = 0;
     b += align_up((size_t)(1u << field) * sizeof(DecMap), 16);  // tables
     b += 256;                                                  // inverses
-    b += align_up((size_t)N * sizeof(int), 16);                // pivrow
+    b += align_up((size_t)N * sizeof(int), 16) * 2;            // pivrow, pcol
     b += align_up((size_t)N, 16) * 2;                          // fsnap, gsnap
     b += (size_t)W;                                            // cur
     if (rows_in_smem) b += (size_t)N * W;
     return b;
+}
+
+// cur[j0 + lane + 32u] ^= sum over stored rows t = warp (mod 16) of
+// f_t * rows[t][same word], u < U; then one atomicXor per word and warp
+template <int U>
+__device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *rows, const uint8_t *fsnap,
+                                               const DecMap *tab, int rank, int nw, int j0, int warp, int lane)
+{
+    uint32_t acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0u;
+    for (int t = warp; t < rank; t += kDecThreads / 32) {
+        const uint32_t f = fsnap[t];
+        if (!f) continue;
+        const ByteMap m = tab[f].m;
+        const uint32_t *row = rows + (size_t)t * nw + j0 + lane;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j0 + lane + 32 * u < nw) acc[u] ^= apply_word(m, row[32 * u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (j0 + lane + 32 * u < nw && acc[u]) atomicXor(&cur[j0 + lane + 32 * u], acc[u]);
 }
 
 __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *__restrict__ gens)
@@ -73,7 +97,9 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     p += align_up((size_t)q * sizeof(DecMap), 16);
     uint8_t *invt = p;
     p += 256;
-    int *pivrow = reinterpret_cast<int *>(p);
+    int *pivrow = reinterpret_cast<int *>(p);  // pivot column -> stored row
+    p += align_up((size_t)N * sizeof(int), 16);
+    int *pcol = reinterpret_cast<int *>(p);    // stored row -> pivot column
     p += align_up((size_t)N * sizeof(int), 16);
     uint8_t *fsnap = p;
     p += align_up((size_t)N, 16);
@@ -123,33 +149,22 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
             cur[j] = v;
         }
         __syncthreads();
-        // 2. pivot-column values of the arriving row
-        for (int i = tid; i < N; i += blockDim.x) fsnap[i] = pivrow[i] >= 0 ? curb[i] : 0;
+        // 2. the arriving row's value in the pivot column of each stored row
+        for (int t = tid; t < rank; t += blockDim.x) fsnap[t] = curb[pcol[t]];
         __syncthreads();
-        // 3. cur -= sum_p f_p * row(p): stored rows are reduced, so every f_p is
-        //    the arriving row's own value in column p.  Warp w takes the pivot
-        //    columns p = w (mod 8); each lane accumulates four word columns of a
-        //    128-word chunk in registers (independent chains), then one
-        //    atomicXor per word and warp combines the warps' partial sums.
+        // 3. cur -= sum_t f_t * row(t): stored rows are reduced, so every f_t is
+        //    the arriving row's own value in row t's pivot column.  Warp w takes
+        //    the stored rows t = w (mod 16); each lane accumulates its word
+        //    columns (up to four, as many as the row is wide, in independent
+        //    registers) and one atomicXor per word and warp combines the warps.
         if (rank > 0) {
+            const int wpl = (nw + 31) / 32;  // words per lane
             for (int j0 = 0; j0 < nw; j0 += 128) {
-                uint32_t acc[4] = {0u, 0u, 0u, 0u};
-                for (int pc = warp; pc < N; pc += kDecThreads / 32) {
-                    const uint32_t f = fsnap[pc];
-                    if (!f) continue;
-                    const ByteMap m = tab[f].m;
-                    const uint32_t *row = rows + (size_t)pivrow[pc] * nw;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = j0 + lane + 32 * u;
-                        if (j < nw) acc[u] ^= apply_word(m, row[j]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + lane + 32 * u;
-                    if (j < nw && acc[u]) atomicXor(&cur[j], acc[u]);
-                }
+                const int left = min(4, (nw - j0 + 31) / 32);
+                if (wpl >= 4 && left == 4) eliminate_rows<4>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
+                else if (left == 3) eliminate_rows<3>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
+                else if (left == 2) eliminate_rows<2>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
+                else eliminate_rows<1>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
             }
         }
         __syncthreads();
@@ -209,6 +224,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         __syncthreads();
         if (tid == 0) {
             pivrow[piv] = rank;
+            pcol[rank] = piv;
             s_rank = rank + 1;
         }
         __syncthreads();
