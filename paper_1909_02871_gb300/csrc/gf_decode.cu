@@ -374,7 +374,14 @@ size_t decode_stage_bytes(const DecodeWork &w)
 size_t stage_decode(DecodeWork &w, char *host, char *dev_base, size_t off, WorkCounter *counters)
 {
     const size_t gb = w.gens.size() * sizeof(DecGen);
-    memcpy(host + off, w.gens.data(), gb);
+    // one CTA per generation, scheduled roughly in block order: the most
+    // expensive eliminations (N^2 (N + R) row operations) go first so that
+    // none of them starts near the end of the launch
+    std::vector<DecGen> order(w.gens);
+    std::stable_sort(order.begin(), order.end(), [](const DecGen &a, const DecGen &b) {
+        return (double)a.N * a.N * (a.N + a.R) > (double)b.N * b.N * (b.N + b.R);
+    });
+    memcpy(host + off, order.data(), gb);
     w.d_gens = reinterpret_cast<DecGen *>(dev_base + off);
     off += align_up(gb, 256);
     for (size_t i = 0; i < w.batches.size(); ++i) {
