@@ -119,6 +119,32 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# whole-job aggregation over ranks (one replica per GPU, no data-path collective)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, device) -> float:
+    """The largest `x` over all ranks (the job's time is its slowest rank's);
+    `x` itself without an initialised process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, steps: int, total_ms: float) -> float:
+    """Units all ranks processed per second over the max-over-ranks time."""
+    return world * units_per_rank * steps / (total_ms / 1e3)
+
+
+def rank_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
 # reference arm / cpu baseline: the oracle on the host cores
 # ---------------------------------------------------------------------------
 def oracle_encode_rate(batch, budget_s: float, max_gens: int | None = None):
@@ -191,11 +217,6 @@ def run_gf(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     launches_per_step = plan.kernel_count
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     # warm-up
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -204,7 +225,7 @@ def run_gf(args, rank, world, local_rank):
 
     # timed region: per-step events on the launching stream
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
+    rank_barrier()
     torch.cuda.synchronize()
     with Clocks(local_rank) as clk:
         with torch.cuda.stream(stream):
@@ -214,16 +235,11 @@ def run_gf(args, rank, world, local_rank):
                 ev[s + 1].record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
-    barrier()
+    rank_barrier()
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
     out_bytes = N_GENS * N_CODED * LEN
-    value = world * out_bytes * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_rate(out_bytes, world, args.steps, total_ms) / 1e9
     ms_per_step = total_ms / args.steps
     clocks = clk.summary()
 
@@ -386,6 +402,8 @@ def run_uneven(args, rank, world, local_rank):
         step.replay()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    rank_barrier()
+    torch.cuda.synchronize()
     with Clocks(local_rank) as clk:
         with torch.cuda.stream(stream):
             ev[0].record(stream)
@@ -393,8 +411,10 @@ def run_uneven(args, rank, world, local_rank):
                 step.replay()
                 ev[i + 1].record(stream)
         stream.synchronize()
+    torch.cuda.synchronize()
+    rank_barrier()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), dev)
     bad = [i for i in (0, 1, len(batch.gens) // 2, len(batch.gens) - 1)
            if not np.array_equal(pipeline.decoded(work, i), batch.gens[i].src)]
     # plain form on a subset, extrapolated by source bytes
@@ -406,7 +426,7 @@ def run_uneven(args, rank, world, local_rank):
         pipeline.plain_step(work, sub, stream=stream)
     stream.synchronize()
     plain_s = time.perf_counter() - t0
-    value = work.bytes_src * args.steps / (total_ms / 1e3) / 1e9
+    value = whole_job_rate(work.bytes_src, world, args.steps, total_ms) / 1e9
     line = {"metric": "uneven encode+decode GB/s (source bytes per step)", "value": value, "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -472,8 +492,9 @@ def run_serve(args, rank, world, local_rank):
     serve.Server(mem_budget=budget).run(reqs[:32])  # warm-up
     reqs = requests(np.zeros(n), 0.0)
     srv = serve.Server(mem_budget=budget)
-    wall = srv.run(reqs)
-    sat = n / wall
+    rank_barrier()
+    wall = max_over_ranks(srv.run(reqs), dev)
+    sat = whole_job_rate(n, world, 1, wall * 1e3)  # every rank serves its own n requests
     ok = all(np.array_equal(r.result, batch.gens[r.rid].src) for r in reqs if isinstance(r, serve.DecodeRequest))
     plain_reqs = requests(np.zeros(n), 0.0)[:64]
     plain_wall = serve.Server(mem_budget=budget, max_active=1).run(plain_reqs)
