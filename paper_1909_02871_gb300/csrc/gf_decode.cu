@@ -35,7 +35,7 @@
 
 namespace gf {
 
-constexpr int kDecThreads = 512;
+constexpr int kDecThreads = 1024;
 
 struct alignas(16) DecMap {
     ByteMap m;
@@ -56,7 +56,7 @@ size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem)
     return b;
 }
 
-// cur[j0 + lane + 32u] ^= sum over stored rows t = warp (mod 16) of
+// cur[j0 + lane + 32u] ^= sum over stored rows t = warp (mod number of warps) of
 // f_t * rows[t][same word], u < U; then one atomicXor per word and warp
 template <int U>
 __device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *rows, const uint8_t *fsnap,
