@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         __syncthreads();
         // 3. cur -= sum_t f_t * row(t): stored rows are reduced, so every f_t is
         //    the arriving row's own value in row t's pivot column.  Warp w takes
-        //    the stored rows t = w (mod 16); each lane accumulates its word
+        //    the stored rows t = w (mod the warp count); each lane accumulates its word
         //    columns (up to four, as many as the row is wide, in independent
         //    registers) and one atomicXor per word and warp combines the warps.
         if (rank > 0) {
