@@ -47,6 +47,7 @@ typedef struct CUstream_st *gf_stream_t;
 #define GF_ETIMEOUT (-5)  /* a device-side wait gave up (reported by gf_device_status) */
 #define GF_ECUDA (-6)     /* a CUDA runtime call or kernel launch failed */
 #define GF_ENOTSUP (-7)   /* the requested path is not available on this device */
+#define GF_EBUSY (-8)     /* the result asked for is not ready yet (gf_dec_status without waiting) */
 
 /* Human-readable name of a status code (static string). */
 const char *gf_strerror(int status);
@@ -208,6 +209,69 @@ int gf_decode_check(const gf_dec_t *gens, int n_gens, gf_stream_t stream);
 #define GF_NOALLOC_SCRATCH_BYTES (256 * 1024)
 int gf_decode_noalloc(int field, int n_src, int n_recv, uint64_t len, const uint8_t *coef, const uint8_t *payload,
                       uint8_t *out, int32_t *rank, int32_t *used, uint8_t *solved, gf_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Resident decoders: packets arrive over time (serving)               */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A decoder keeps one generation's received coded packets in device memory
+ * that the library owns from gf_dec_open until gf_dec_close, so that a
+ * server can append packets as they arrive and decode many partially
+ * received generations in one launch.  The paper describes the encoder only
+ * and has no counterpart; the decode itself is gf_decode_batched's
+ * (progressive Gauss-Jordan in arrival order, stop at rank n_src).  A
+ * decoder is used from one host thread at a time; different decoders are
+ * independent.
+ */
+typedef struct gf_decoder gf_decoder_t;
+
+/* Allocates a decoder for a generation of n_src packets of len bytes in
+ * GF(2^field) that can hold up to max_recv received packets: device buffers
+ * for the coding vectors (max_recv x n_src bytes), the payloads
+ * (max_recv x len) and the decoded packets (n_src x len), from a
+ * library-private stream-ordered pool of the current device that keeps freed
+ * memory for reuse, and a rank word in mapped host memory.  Synchronous.  Errors: GF_EINVAL (field not in
+ * {1,2,4,8}, n_src outside 1..1024, max_recv outside 1..4096, dec NULL),
+ * GF_ENOMEM, GF_ECUDA. */
+int gf_dec_open(int field, int n_src, int max_recv, uint64_t len, gf_decoder_t **dec);
+
+/* Appends n received packets, in arrival order: coef (n x n_src bytes) and
+ * payload (n x len bytes), in host or device memory, copied into the
+ * decoder's buffers with one cudaMemcpyAsync each on `stream` (host memory
+ * must stay valid until the stream has run the copy; pinned memory keeps it
+ * asynchronous).  Errors: GF_EINVAL (NULL pointers with n > 0, n < 0, or
+ * more than max_recv packets in total), GF_ECUDA. */
+int gf_dec_push(gf_decoder_t *dec, const uint8_t *coef, const uint8_t *payload, int n, gf_stream_t stream);
+
+/* Enqueues on `stream` ONE batched decode over every decoder in decs[0..n)
+ * that holds at least n_src packets and has received packets since its
+ * previous attempt; the others are left alone.  The decoded packets overwrite
+ * the decoder's output buffer.  *n_launched (host, may be NULL) receives the
+ * number of decoders attempted.  Asynchronous.  Packets may be pushed (on any
+ * stream) while an attempt runs: they fill rows the attempt does not read.
+ * A decoder must not be polled again before its previous attempt is
+ * complete (gf_dec_status reports it).
+ * Errors: GF_EINVAL, GF_ENOMEM (library workspace), GF_ECUDA. */
+int gf_dec_poll(gf_decoder_t *const *decs, int n, gf_stream_t stream, int *n_launched);
+
+/* Result of the decoder's latest attempt.  With wait != 0 it waits for that
+ * attempt; with wait == 0 it returns GF_EBUSY while the attempt is still
+ * running.  rank: rank reached (-1 if never attempted); received: packets
+ * pushed so far; out: device address of the n_src x len decoded packets
+ * (complete when rank == n_src, valid until gf_dec_close).  Any of the
+ * three may be NULL.  Errors: GF_EINVAL, GF_EBUSY, GF_ECUDA. */
+int gf_dec_status(gf_decoder_t *dec, int wait, int *rank, int *received, const uint8_t **out);
+
+/* Enqueues on `stream` a copy of the decoder's n_src x len decoded packets
+ * (as left by its latest attempt) into dst, host (pinned for asynchrony) or
+ * device memory.  Errors: GF_EINVAL, GF_ECUDA. */
+int gf_dec_read(gf_decoder_t *dec, uint8_t *dst, gf_stream_t stream);
+
+/* Frees the decoder (NULL is a no-op): waits for its latest attempt, then
+ * releases the buffers in stream order after the last push, poll and read
+ * enqueued on any stream, without waiting for those. */
+int gf_dec_close(gf_decoder_t *dec);
 
 /* ------------------------------------------------------------------ */
 /* Plans: pre-uploaded batches for CUDA graph capture                  */

@@ -144,6 +144,7 @@ extern "C" const char *gf_strerror(int status)
     case GF_ETIMEOUT: return "GF_ETIMEOUT: device wait gave up";
     case GF_ECUDA: return "GF_ECUDA: CUDA error";
     case GF_ENOTSUP: return "GF_ENOTSUP: not supported on this device or field";
+    case GF_EBUSY: return "GF_EBUSY: result not ready yet";
     default: return "unknown status";
     }
 }

@@ -16,6 +16,7 @@ import threading
 from . import build as _build
 
 GF_OK, GF_EINVAL, GF_EOVERLAP, GF_ENOMEM, GF_ERANK, GF_ETIMEOUT, GF_ECUDA, GF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+GF_EBUSY = -8
 PATH_AUTO, PATH_TABLE, PATH_BITSLICED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -74,6 +75,15 @@ _SIGS = {
     "gf_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "gf_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "gf_device_status": (ctypes.c_int, []),
+    "gf_dec_open": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "gf_dec_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "gf_dec_poll": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_int)]),
+    "gf_dec_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p)]),
+    "gf_dec_close": (ctypes.c_int, [ctypes.c_void_p]),
+    "gf_dec_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -206,6 +216,57 @@ def gf_decode_noalloc(field: int, n_src: int, n_recv: int, length: int, coef, pa
     device array of the library); returns the raw status."""
     return int(load().gf_decode_noalloc(field, n_src, n_recv, length, _ptr(coef), _ptr(payload), _ptr(out),
                                         _ptr(rank), _ptr(used), _ptr(solved), _stream(stream)))
+
+
+class Decoder:
+    """Owner of a gf_decoder_t: one generation's received packets resident in
+    library-owned device memory (gf_dec_open ... gf_dec_close)."""
+
+    def __init__(self, field: int, n_src: int, max_recv: int, length: int):
+        h = ctypes.c_void_p()
+        _check(load().gf_dec_open(field, n_src, max_recv, length, ctypes.byref(h)), "gf_dec_open")
+        self.handle = h.value
+        self.field, self.n_src, self.max_recv, self.length = field, n_src, max_recv, length
+
+    def push(self, coef, payload, n: int, stream=None) -> None:
+        """Append n packets (coef n x n_src, payload n x len; tensors on the
+        host (pinned) or the device, or raw addresses)."""
+        _check(load().gf_dec_push(self.handle, _ptr(coef), _ptr(payload), n, _stream(stream)), "gf_dec_push")
+
+    @staticmethod
+    def poll(decoders, stream=None) -> int:
+        """One batched decode over every decoder with new packets and at least
+        n_src of them; returns how many were attempted."""
+        arr = (ctypes.c_void_p * max(len(decoders), 1))(*[d.handle for d in decoders])
+        k = ctypes.c_int()
+        _check(load().gf_dec_poll(arr, len(decoders), _stream(stream), ctypes.byref(k)), "gf_dec_poll")
+        return k.value
+
+    def status(self, wait: bool = True):
+        """(rank, received, device address of the decoded packets), or None
+        while the latest attempt is still running (wait=False)."""
+        r, n, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+        st = load().gf_dec_status(self.handle, 1 if wait else 0, ctypes.byref(r), ctypes.byref(n), ctypes.byref(o))
+        if st == GF_EBUSY:
+            return None
+        _check(st, "gf_dec_status")
+        return r.value, n.value, o.value
+
+    def read(self, dst, stream=None) -> None:
+        """Enqueue a copy of the n_src x len decoded packets into dst (tensor
+        on the host, pinned, or the device)."""
+        _check(load().gf_dec_read(self.handle, _ptr(dst), _stream(stream)), "gf_dec_read")
+
+    def close(self) -> None:
+        if self.handle:
+            h, self.handle = self.handle, None
+            _check(load().gf_dec_close(h), "gf_dec_close")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

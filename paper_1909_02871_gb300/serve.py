@@ -9,11 +9,12 @@ Requests arrive over time (Poisson arrivals in the benchmark):
   determine all N sources (rank N) and returns them.
 
 The loop admits waiting requests while device memory (a fixed budget) and
-request slots allow, copies newly arrived packets of admitted decode requests
-into their device-resident buffers (partially received generations stay on
-the GPU), and launches, on the next of several CUDA streams, ONE batched
-encode for every admitted encode request and ONE batched decode for every
-decode request holding at least N packets it has not tried with.  It does
+request slots allow, appends newly arrived packets of admitted decode requests
+to their resident decoders (gf_dec_open / gf_dec_push: partially received
+generations stay on the GPU in library-owned memory), and launches, on the
+next of several CUDA streams, ONE batched encode for every admitted encode
+request and ONE batched decode (gf_dec_poll) for every decoder holding at
+least N packets it has not tried with.  It does
 not wait for the launch: later requests are admitted and launched on another
 stream while earlier batches run, so their work overlaps on the device.
 Finished batches are found by polling their CUDA events; a decode that came
@@ -108,28 +109,27 @@ class Server:
 
     def _admit_decode(self, r: DecodeRequest):
         R = r.coef.shape[0]
-        r.dev = {"coef": self._alloc(R * r.n_src), "payload": self._alloc(R * r.length),
-                 "out": self._alloc(r.n_src * r.length),
-                 "rank": self.torch.zeros(1, dtype=self.torch.int32, device=self.dev),
+        r.dev = {"dec": gf.Decoder(r.field, r.n_src, R, r.length),
                  "coef_h": self._pinned(r.coef), "pay_h": self._pinned(r.payload)}
 
     def _feed(self, r: DecodeRequest, upto: int):
-        """Copy packets [received, upto) of a decode request to its resident
-        device buffers (on the copy stream)."""
+        """Append packets [received, upto) of a decode request to its resident
+        decoder (on the copy stream; an attempt in flight reads only the rows
+        before `tried`, so the appended rows do not disturb it)."""
         if upto <= r.received:
             return
         N, L = r.n_src, r.length
-        a, b = r.received * N, upto * N
-        if b > a:
-            r.dev["coef"][a:b].copy_(r.dev["coef_h"][a:b], non_blocking=True)
-        a, b = r.received * L, upto * L
-        if b > a:
-            r.dev["payload"][a:b].copy_(r.dev["pay_h"][a:b], non_blocking=True)
+        n = upto - r.received
+        coef = r.dev["coef_h"].data_ptr() + r.received * N
+        pay = r.dev["pay_h"].data_ptr() + r.received * L
+        r.dev["dec"].push(coef, pay, n, stream=self.copy_stream)
         r.received = upto
 
     def _finish(self, r, t):
         r.done_at = t
         self.mem_used -= r.device_bytes()
+        if "dec" in r.dev:
+            r.dev["dec"].close()
         r.dev = {}
 
     # ------------------------------------------------------------------
@@ -181,9 +181,7 @@ class Server:
                                              stream=stream)
                         self.launches += 1
                     if ready_dec:
-                        gf.gf_decode_batched([(r.field, r.n_src, r.received, r.length, r.dev["coef"],
-                                               r.dev["payload"], r.dev["out"], r.dev["rank"], None, None)
-                                              for r in ready_dec], stream=stream)
+                        gf.Decoder.poll([r.dev["dec"] for r in ready_dec], stream=stream)
                         self.launches += 1
                     for r in pending_enc:
                         h = torch.empty(r.dev["out"].numel(), dtype=torch.uint8, pin_memory=True)
@@ -192,11 +190,9 @@ class Server:
                     for r in ready_dec:
                         r.tried = r.received
                         r.busy = True
-                        h = torch.empty(r.dev["out"].numel(), dtype=torch.uint8, pin_memory=True)
-                        h.copy_(r.dev["out"], non_blocking=True)
-                        hr = torch.empty(1, dtype=torch.int32, pin_memory=True)
-                        hr.copy_(r.dev["rank"], non_blocking=True)
-                        copies.append((h, hr))
+                        h = torch.empty(max(r.n_src * r.length, 1), dtype=torch.uint8, pin_memory=True)
+                        r.dev["dec"].read(h, stream=stream)
+                        copies.append(h)
                     ev = torch.cuda.Event()
                     ev.record(stream)
                 inflight.append((ev, pending_enc, ready_dec, copies))
@@ -215,9 +211,9 @@ class Server:
                     r.result = h.numpy()[:K * L].reshape(K, L).copy()
                     self._finish(r, t)
                     remaining -= 1
-                for r, (h, hr) in zip(decs, copies[len(encs):]):
+                for r, h in zip(decs, copies[len(encs):]):
                     r.busy = False
-                    r.rank = int(hr.numpy()[0])
+                    r.rank = r.dev["dec"].status(wait=True)[0]  # the attempt is complete: no wait
                     if r.rank == r.n_src:
                         r.result = h.numpy()[:r.n_src * r.length].reshape(r.n_src, r.length).copy()
                     elif not (r.received >= r.coef.shape[0] and r.received == r.tried):

@@ -68,3 +68,22 @@ def test_empty_batches_are_noops(n_gens):
     assert lib.gf_encode_batched_ex(arr, n_gens, 0, None) == gf.GF_OK
     darr = (gf.GfDec * 1)()
     assert lib.gf_decode_batched(darr, n_gens, None) == gf.GF_OK
+
+
+def test_decoder_host_side_errors_without_gpu():
+    """The resident-decoder entry points check their arguments first."""
+    import ctypes
+    from paper_1909_02871_gb300 import gf
+    lib = gf.load()
+    h = ctypes.c_void_p()
+    assert lib.gf_dec_open(3, 16, 32, 100, ctypes.byref(h)) == gf.GF_EINVAL   # bad field
+    assert lib.gf_dec_open(8, 0, 32, 100, ctypes.byref(h)) == gf.GF_EINVAL    # n_src < 1
+    assert lib.gf_dec_open(8, 16, 5000, 100, ctypes.byref(h)) == gf.GF_EINVAL  # max_recv too large
+    assert lib.gf_dec_open(8, 16, 32, 100, None) == gf.GF_EINVAL
+    k = ctypes.c_int(7)
+    assert lib.gf_dec_poll(None, -1, None, ctypes.byref(k)) == gf.GF_EINVAL and k.value == 0
+    assert lib.gf_dec_poll(None, 0, None, ctypes.byref(k)) == gf.GF_OK and k.value == 0
+    assert lib.gf_dec_status(None, 1, None, None, None) == gf.GF_EINVAL
+    assert lib.gf_dec_push(None, None, None, 1, None) == gf.GF_EINVAL
+    assert lib.gf_dec_close(None) == gf.GF_OK
+    assert gf.strerror(gf.GF_EBUSY) != "unknown status"
