@@ -521,13 +521,144 @@ def run_serve(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_region_sweep(args, rank, world, local_rank):
+    """Region madd / mul over 2^10 .. 2^30 bytes in GF(2), GF(4), GF(16),
+    GF(256): HBM GB/s (3 bytes moved per region byte for madd, 2 for mul)
+    against the measured copy bandwidth.  Regions that fit in L2 are timed
+    one call at a time with L2 flushed (a 256 MB write) before each call."""
+    import torch
+
+    from paper_1909_02871_gb300 import gf
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    hbm_peak, _, peak_kind = _peaks()
+    stream = torch.cuda.Stream(device=dev)
+    n_max = 1 << 30
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    a = torch.randint(0, 256, (n_max,), dtype=torch.uint8, device=dev, generator=g)
+    b = torch.randint(0, 256, (n_max,), dtype=torch.uint8, device=dev, generator=g)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    l2_bytes = 128 << 20
+    points = []
+    launches = 0  # timed region-op launches (one kernel each)
+    crng = np.random.default_rng(1909)
+    rank_barrier()
+    with Clocks(local_rank) as clk, torch.cuda.stream(stream):
+        for field in (1, 2, 4, 8):
+            for op, fn, per in (("madd", gf.gf_region_madd, 3), ("mul", gf.gf_region_mul, 2)):
+                for e in range(10, 31):
+                    n = 1 << e
+                    c = int(crng.integers(1, 1 << field)) if field > 1 else 1
+                    for _ in range(3):
+                        fn(field, b, a, c, length=n, stream=stream)
+                    cold = per * n <= 2 * l2_bytes
+                    reps = 5 if cold else max(3, min(50, (1 << 33) // (per * n)))
+                    times = []
+                    for _ in range(reps):
+                        if cold:
+                            flush.fill_(1)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fn(field, b, a, c, length=n, stream=stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                    ms = statistics.median(times)
+                    gbs = per * n / (ms / 1e3) / 1e9
+                    points.append({"field": field, "op": op, "len": n, "coef": c, "us": ms * 1e3,
+                                   "GBps_hbm": gbs, "frac": gbs / hbm_peak, "l2_flushed": cold})
+                    launches += reps
+    stream.synchronize()
+    big = [p for p in points if p["len"] == n_max]
+    line = {"metric": "region madd/mul HBM GB/s (sweep)", "value": min(p["GBps_hbm"] for p in big), "unit": "GB/s",
+            "n_gpus": world, "steps": len(points), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "region madd/mul, len 2^10..2^30 B, GF(2), GF(4), GF(16), GF(256), random "
+                                   "nonzero coefficient per point; regions up to 2 x L2 timed with L2 flushed",
+                       "value_is": "the lowest of the eight 1 GiB points"},
+            "peak": hbm_peak, "peak_kind": peak_kind, "clocks": clk.summary(), "points": points,
+            "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_single(args, rank, world, local_rank):
+    """One generation (N = 16 sources of 1500 B, K = 16 coded packets) per
+    call in each field: device time and host-call time of one encode and of
+    one decode of the 16 packets, each checked against the oracle."""
+    import torch
+
+    import oracle
+    from paper_1909_02871_gb300 import gf, synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    ok = True
+    reps = 200
+    rank_barrier()
+    with Clocks(local_rank) as clk:
+        for field in (1, 2, 4, 8):
+            gen = synth.generation(field)
+            coef_np = np.ascontiguousarray(gen.coef_stream[:gen.n_coded])
+            N, K, L = gen.n_src, coef_np.shape[0], gen.length
+            src = torch.from_numpy(gen.src).to(dev)
+            coef = torch.from_numpy(coef_np).to(dev)
+            out = torch.empty((K, L), dtype=torch.uint8, device=dev)
+            dec_out = torch.empty((N, L), dtype=torch.uint8, device=dev)
+            rnk = torch.zeros(1, dtype=torch.int32, device=dev)
+            enc = [(field, N, K, L, src, coef, out)]
+            decs = [(field, N, K, L, coef, out, dec_out, rnk, None, None)]
+            timings = {}
+            for name, call in (("encode", lambda: gf.gf_encode_batched(enc, stream=stream)),
+                               ("decode", lambda: gf.gf_decode_batched(decs, stream=stream))):
+                for _ in range(5):
+                    call()
+                stream.synchronize()
+                dev_us, host_us = [], []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    t0 = time.perf_counter()
+                    e0.record(stream)
+                    call()
+                    e1.record(stream)
+                    e1.synchronize()
+                    host_us.append((time.perf_counter() - t0) * 1e6)
+                    dev_us.append(e0.elapsed_time(e1) * 1e3)
+                timings[name] = {"device_us_p50": statistics.median(dev_us),
+                                 "device_us_p99": float(np.percentile(dev_us, 99)),
+                                 "call_us_p50": statistics.median(host_us)}
+            coded = out.cpu().numpy()
+            good = np.array_equal(coded, oracle.encode(field, gen.src, coef_np))
+            rank_ok = int(rnk.item())
+            if rank_ok == N:
+                good = good and np.array_equal(dec_out.cpu().numpy(), gen.src)
+            ok = ok and good
+            timings["rank"] = rank_ok
+            timings["bit_exact"] = bool(good)
+            res[f"GF(2^{field})"] = timings
+    enc_us = res["GF(2^8)"]["encode"]["device_us_p50"]
+    line = {"metric": "single generation encode/decode latency (us)", "value": enc_us, "unit": "us",
+            "n_gpus": world, "steps": reps, "warmup": 5, "ms_per_step": enc_us / 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "one generation: N=16 x 1500 B, K=16, four fields, one call per encode and "
+                                   "per decode", "value_is": "GF(256) encode, device time, median"},
+            "fields": res, "round_trip_ok": ok, "clocks": clk.summary(),
+            "gpu_launches": 4 * reps * 3}  # per field and rep: one encode kernel, two decode kernels
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
-    ap.add_argument("--workload", choices=["uniform", "uneven", "serve"], default="uniform")
+    ap.add_argument("--workload", choices=["uniform", "uneven", "serve", "region", "single"], default="uniform")
     ap.add_argument("--gens", type=int, default=2048, help="generations of the uneven workload")
     ap.add_argument("--requests", type=int, default=600, help="requests of the serving workload")
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
@@ -557,6 +688,10 @@ def main():
         run_uneven(args, rank, world, local_rank)
     elif args.workload == "serve":
         run_serve(args, rank, world, local_rank)
+    elif args.workload == "region":
+        run_region_sweep(args, rank, world, local_rank)
+    elif args.workload == "single":
+        run_single(args, rank, world, local_rank)
     else:
         run_gf(args, rank, world, local_rank)
     if world > 1 and args.impl == "gf":
