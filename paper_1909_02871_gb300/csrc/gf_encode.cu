@@ -246,6 +246,19 @@ void finalize_batch(EncodeBatch &b)
 {
     b.tile_start.assign(b.gens.size() + 1, 0);
     b.all_gf256 = true;
+    if (b.kind == GF_PATH_BITSLICED) {
+        // a bit-sliced work item is (generation, 64 coded packets) over all its
+        // column tiles; a batch with fewer items than about two per SM splits
+        // each item's column tiles into ranges so that the SMs all get work
+        long long items = 0;
+        for (const EncGen &g : b.gens) items += (g.n_coded + 63) / 64;
+        const long long want = 2LL * sm_count();
+        const long long split = items > 0 && items < want ? (want + items - 1) / items : 1;
+        for (EncGen &g : b.gens) {
+            const long long ncols = (long long)((g.len + 127) / 128);
+            g.col_chunks = (int)std::max(1LL, std::min(split, ncols));
+        }
+    }
     long long t = 0;
     for (size_t i = 0; i < b.gens.size(); ++i) {
         b.tile_start[i] = t;

@@ -106,6 +106,7 @@ struct Ctl {
     long long ring_item[2];
     EncGen ring_gen[2];  // generation record of each published item
     int ring_k0[2];      // its first coded packet
+    int ring_c0[2], ring_c1[2];  // its column tiles [c0, c1)
     uint32_t tmem_base;
     int abort;
 };
@@ -472,8 +473,14 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 if (!ok) ctl->abort = 1;
                 if (it != kSentinel) {
                     const int gi = locate(tile_start, n_gens, it);
-                    ctl->ring_gen[e] = gens[gi];
-                    ctl->ring_k0[e] = (int)(it - __ldg(tile_start + gi)) * kCodedPerItem;
+                    const EncGen gg = gens[gi];
+                    const long long local = it - __ldg(tile_start + gi);
+                    const int split = gg.col_chunks, cs = (int)(local % split);
+                    const int ncols = (int)((gg.len + kColTile - 1) / kColTile);
+                    ctl->ring_gen[e] = gg;
+                    ctl->ring_k0[e] = (int)(local / split) * kCodedPerItem;
+                    ctl->ring_c0[e] = (int)((long long)cs * ncols / split);
+                    ctl->ring_c1[e] = (int)((long long)(cs + 1) * ncols / split);
                 }
                 ring[e] = it;
                 mbar_arrive(&ctl->info_full[e]);
@@ -558,10 +565,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             }
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
+            const int c0 = ctl->ring_c0[e];
+            const int ncols = ctl->ring_c1[e] - c0;  // column tiles c0 .. c0+ncols-1 of the generation
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
             // units = (64-source chunk, column tile), chunk-major: the order the MMAs consume A
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
@@ -570,7 +578,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 for (int p = 0; p < kStages - 1; ++p) {
                     if (p < nunits) {
                         const int kc = p / ncols;
-                        stage_tile(stage_lane(g, kc * kMaxSrc + ibase, quarter, lane), p - kc * ncols,
+                        stage_tile(stage_lane(g, kc * kMaxSrc + ibase, quarter, lane), c0 + p - kc * ncols,
                                    stage + p * kStageBytes);
                     } else {
                         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -585,7 +593,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     const int vs = v + kStages - 1;
                     if (vs < nunits) {
                         const int kcs = vs / ncols;
-                        stage_tile(stage_lane(g, kcs * kMaxSrc + ibase, quarter, lane), vs - kcs * ncols,
+                        stage_tile(stage_lane(g, kcs * kMaxSrc + ibase, quarter, lane), c0 + vs - kcs * ncols,
                                    stage + (vs % kStages) * kStageBytes);
                     } else {
                         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -612,8 +620,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 #pragma unroll
                             for (int t = 0; t < 8; ++t) b[t] = sb[((2 * half + grp) * 8 + t) * 32];
                         } else {
-                            load_direct(g, kc * kMaxSrc + ibase, (unsigned long long)ct * kColTile + pos, b,
-                                        2 * half + grp);
+                            load_direct(g, kc * kMaxSrc + ibase, (unsigned long long)(c0 + ct) * kColTile + pos,
+                                        b, 2 * half + grp);
                         }
 #pragma unroll
                         for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread[b[t]];
@@ -645,11 +653,12 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
             const int k0i = ctl->ring_k0[e];
+            const int c0 = ctl->ring_c0[e];
+            const int ncols = ctl->ring_c1[e] - c0;  // column tiles c0 .. c0+ncols-1 of the generation
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const unsigned long long len = g.len;
-            const int ncols = (int)((len + kColTile - 1) / kColTile);
             const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             bool ok = true;
@@ -679,8 +688,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     outb[t] = parity_byte(va + 4 * t);
                     outb[4 + t] = parity_byte(vb + 4 * t);
                 }
-                if ((unsigned long long)ct * kColTile + pos < len && nk > 0) {
-                    uint8_t *o = g.out + (size_t)k0 * len + (size_t)ct * kColTile + pos;
+                if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nk > 0) {
+                    uint8_t *o = g.out + (size_t)k0 * len + (size_t)(c0 + ct) * kColTile + pos;
                     if (first) {
 #pragma unroll
                         for (int kp = 0; kp < 8; ++kp) {
@@ -713,11 +722,12 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             }
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
+            const int k0i = ctl->ring_k0[e];
+            const int ncols = ctl->ring_c1[e] - ctl->ring_c0[e];  // column tiles of this item
             mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const int ncols = (int)((g.len + kColTile - 1) / kColTile);
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
-            const int nh = (min(kCodedPerItem, g.n_coded - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
+            const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
             bool ok = true;
             for (int v = 0; v < nunits && ok; ++v) {
                 const int kc = v / ncols, ct = v - kc * ncols;  // 64-source chunk, column tile
@@ -828,9 +838,9 @@ long long bitsliced_tiles(const EncGen &g, int &col_chunks, int &k_chunks)
         col_chunks = k_chunks = 0;
         return 0;
     }
-    col_chunks = 1;
+    if (col_chunks < 1) col_chunks = 1;  // column ranges per item (set by the batch planner)
     k_chunks = (g.n_coded + tc::kCodedPerItem - 1) / tc::kCodedPerItem;
-    return k_chunks;
+    return (long long)k_chunks * col_chunks;
 }
 
 int launch_bitsliced(const EncodeBatch &b, cudaStream_t stream)
