@@ -254,9 +254,11 @@ void finalize_batch(EncodeBatch &b)
         for (const EncGen &g : b.gens) items += (g.n_coded + 63) / 64;
         const long long want = 2LL * sm_count();
         const long long split = items > 0 && items < want ? (want + items - 1) / items : 1;
+        b.col_split = false;
         for (EncGen &g : b.gens) {
             const long long ncols = (long long)((g.len + 127) / 128);
             g.col_chunks = (int)std::max(1LL, std::min(split, ncols));
+            if (g.col_chunks > 1) b.col_split = true;
         }
     }
     long long t = 0;

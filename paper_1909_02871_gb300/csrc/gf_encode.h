@@ -39,6 +39,7 @@ struct EncodeBatch {
     std::vector<long long> tile_start;  // n_gens + 1 prefix sums
     long long total_tiles = 0;
     bool all_gf256 = true;  // bit-sliced: every generation is GF(256) (specialised kernel)
+    bool col_split = false;  // bit-sliced: some item covers only a range of its column tiles
     // device copies (inside a workspace or plan buffer)
     WorkCounter *d_counter = nullptr;
     EncGen *d_gens = nullptr;

@@ -355,7 +355,9 @@ __device__ __forceinline__ uint32_t b_chunk(int n, int kb, int m)
 
 // kAnyField = false: every generation of the launch is GF(256) (only that
 // table is built and the B builder indexes it directly); true: any field.
-template <bool kAnyField>
+// kColSplit = false: every item covers all column tiles of its generation;
+// true: items cover column ranges (small batches).
+template <bool kAnyField, bool kColSplit>
 __global__ void __launch_bounds__(kThreads, 1)
 encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__restrict__ tile_start, int n_gens,
                         long long total, WorkCounter *ctr, int *status)
@@ -474,13 +476,20 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 if (it != kSentinel) {
                     const int gi = locate(tile_start, n_gens, it);
                     const EncGen gg = gens[gi];
-                    const long long local = it - __ldg(tile_start + gi);
-                    const int split = gg.col_chunks, cs = (int)(local % split);
+                    const int local = (int)(it - __ldg(tile_start + gi));  // item within the generation
+                    const int split = gg.col_chunks;
                     const int ncols = (int)((gg.len + kColTile - 1) / kColTile);
                     ctl->ring_gen[e] = gg;
-                    ctl->ring_k0[e] = (int)(local / split) * kCodedPerItem;
-                    ctl->ring_c0[e] = (int)((long long)cs * ncols / split);
-                    ctl->ring_c1[e] = (int)((long long)(cs + 1) * ncols / split);
+                    if (!kColSplit || split == 1) {  // the whole row of column tiles (large batches)
+                        ctl->ring_k0[e] = local * kCodedPerItem;
+                        ctl->ring_c0[e] = 0;
+                        ctl->ring_c1[e] = ncols;
+                    } else {
+                        const int kq = local / split, cs = local - kq * split;
+                        ctl->ring_k0[e] = kq * kCodedPerItem;
+                        ctl->ring_c0[e] = (int)((long long)cs * ncols / split);
+                        ctl->ring_c1[e] = (int)((long long)(cs + 1) * ncols / split);
+                    }
                 }
                 ring[e] = it;
                 mbar_arrive(&ctl->info_full[e]);
@@ -565,8 +574,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             }
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
-            const int c0 = ctl->ring_c0[e];
-            const int ncols = ctl->ring_c1[e] - c0;  // column tiles c0 .. c0+ncols-1 of the generation
+            const int c0 = kColSplit ? ctl->ring_c0[e] : 0;
+            // column tiles c0 .. c0+ncols-1 of the generation
+            const int ncols = kColSplit ? ctl->ring_c1[e] - c0 : (int)((g.len + kColTile - 1) / kColTile);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
@@ -653,8 +663,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
             const int k0i = ctl->ring_k0[e];
-            const int c0 = ctl->ring_c0[e];
-            const int ncols = ctl->ring_c1[e] - c0;  // column tiles c0 .. c0+ncols-1 of the generation
+            const int c0 = kColSplit ? ctl->ring_c0[e] : 0;
+            // column tiles c0 .. c0+ncols-1 of the generation
+            const int ncols = kColSplit ? ctl->ring_c1[e] - c0 : (int)((g.len + kColTile - 1) / kColTile);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
@@ -723,7 +734,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const long long item = ring[e];
             const EncGen g = ctl->ring_gen[e];
             const int k0i = ctl->ring_k0[e];
-            const int ncols = ctl->ring_c1[e] - ctl->ring_c0[e];  // column tiles of this item
+            // column tiles of this item
+            const int ncols = kColSplit ? ctl->ring_c1[e] - ctl->ring_c0[e] : (int)((g.len + kColTile - 1) / kColTile);
             mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
@@ -851,10 +863,14 @@ int launch_bitsliced(const EncodeBatch &b, cudaStream_t stream)
         std::lock_guard<std::mutex> lock(mu);
         const int dev = current_device();
         if (dev != configured_dev) {
-            if (cudaFuncSetAttribute(tc::encode_bitsliced_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tc::kSmemBytes) != cudaSuccess ||
-                cudaFuncSetAttribute(tc::encode_bitsliced_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tc::kSmemBytes) != cudaSuccess)
+            if (cudaFuncSetAttribute(tc::encode_bitsliced_kernel<false, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(tc::encode_bitsliced_kernel<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(tc::encode_bitsliced_kernel<false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes) != cudaSuccess ||
+                cudaFuncSetAttribute(tc::encode_bitsliced_kernel<true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes) != cudaSuccess)
                 return GF_ECUDA;
             configured_dev = dev;
         }
@@ -862,12 +878,12 @@ int launch_bitsliced(const EncodeBatch &b, cudaStream_t stream)
     int *status = device_status_word();
     if (!status) return GF_ENOMEM;
     const long long grid = std::min<long long>(b.total_tiles, sm_count());
-    if (b.all_gf256)
-        tc::encode_bitsliced_kernel<false><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(
-            b.d_gens, b.d_tile_start, (int)b.gens.size(), b.total_tiles, b.d_counter, status);
-    else
-        tc::encode_bitsliced_kernel<true><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(
-            b.d_gens, b.d_tile_start, (int)b.gens.size(), b.total_tiles, b.d_counter, status);
+    auto kern = b.all_gf256 ? (b.col_split ? tc::encode_bitsliced_kernel<false, true>
+                                           : tc::encode_bitsliced_kernel<false, false>)
+                            : (b.col_split ? tc::encode_bitsliced_kernel<true, true>
+                                           : tc::encode_bitsliced_kernel<true, false>);
+    kern<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, stream>>>(b.d_gens, b.d_tile_start, (int)b.gens.size(),
+                                                                   b.total_tiles, b.d_counter, status);
     return cuda_status(cudaGetLastError());
 }
 
