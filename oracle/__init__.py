@@ -68,6 +68,9 @@ def _load():
         lib.gfo_decode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p,
                                    u8p, ctypes.POINTER(ctypes.c_int)]
         lib.gfo_decode.restype = ctypes.c_int
+        lib.gfo_recode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p, u8p,
+                                   u8p]
+        lib.gfo_recode.restype = None
         lib.gfo_rank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
         lib.gfo_rank.restype = ctypes.c_int
         _lib = lib
@@ -192,3 +195,27 @@ def rank(n: int, coef: np.ndarray) -> int:
     R, N = coef.shape
     _check_field(n)
     return int(_load().gfo_rank(n, R, N, _u8(coef) if coef.size else _u8(np.zeros(1, np.uint8))))
+
+
+def recode(n: int, coef_in: np.ndarray, payload_in: np.ndarray, mix: np.ndarray):
+    """Recoding at an intermediate node: K2 new packets, each a combination
+    (coefficients mix, K2 x R) of the R coded packets held (coef_in R x N,
+    payload_in R x len).  Returns (coef_out K2 x N, payload_out K2 x len)."""
+    coef_in = np.ascontiguousarray(coef_in, dtype=np.uint8)
+    payload_in = np.ascontiguousarray(payload_in, dtype=np.uint8)
+    mix = np.ascontiguousarray(mix, dtype=np.uint8)
+    R, N = coef_in.shape
+    K2, R2 = mix.shape
+    assert R == R2 and payload_in.shape[0] == R
+    L = payload_in.shape[1]
+    _check_field(n)
+    for a in (coef_in, mix):
+        if a.size and int(a.max()) >= (1 << n):
+            raise ValueError("coefficient outside the field")
+    coef_out = np.zeros((K2, N), dtype=np.uint8)
+    payload_out = np.zeros((K2, L), dtype=np.uint8)
+    z = np.zeros(1, np.uint8)
+    _load().gfo_recode(n, N, R, K2, L, _u8(coef_in) if coef_in.size else _u8(z),
+                       _u8(payload_in) if payload_in.size else _u8(z), _u8(mix) if mix.size else _u8(z),
+                       _u8(coef_out) if coef_out.size else _u8(z), _u8(payload_out) if payload_out.size else _u8(z))
+    return coef_out, payload_out

@@ -313,3 +313,29 @@ int gfo_rank(int n, int R, int N, const uint8_t *coef)
     free(out); free(solved);
     return rank;
 }
+
+/* ------------------------------------------------------------------ */
+/* Recoding at an intermediate node (section II: a node forwards linear */
+/* combinations of the packets it has received)                        */
+/* ------------------------------------------------------------------ */
+
+/* A node holding R coded packets (coding vectors coef_in, R x N; payloads
+ * payload_in, R x len) sends K2 new ones, each a linear combination of the
+ * packets it holds with fresh coefficients mix (K2 x R):
+ *   payload_out_k = sum_r mix[k][r] * payload_in_r        (Eq. 2 again)
+ *   coef_out_k[i] = sum_r mix[k][r] * coef_in[r][i]       (field products)
+ * so that coef_out expresses the new packets in the original sources. */
+void gfo_recode(int n, int N, int R, int K2, size_t len, const uint8_t *coef_in,
+                const uint8_t *payload_in, const uint8_t *mix, uint8_t *coef_out,
+                uint8_t *payload_out)
+{
+    int k, r, i;
+    for (k = 0; k < K2; k++)
+        for (i = 0; i < N; i++) {
+            unsigned acc = 0;
+            for (r = 0; r < R; r++)
+                acc ^= gfo_mul(n, mix[(size_t)k * R + r], coef_in[(size_t)r * N + i]);
+            coef_out[(size_t)k * N + i] = (uint8_t)acc;
+        }
+    gfo_encode(n, R, K2, len, payload_in, mix, payload_out);
+}

@@ -156,3 +156,60 @@ def test_uneven_generation_round_trip(n):
         out, solved, rank, used = oracle.decode(n, ge.coef_stream[keep], coded[keep])
         assert rank == ge.n_src and solved.all()
         assert np.array_equal(out, ge.src)
+
+
+# ---------------------------------------------------------------------------
+# recoding at an intermediate node (oracle.recode)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", FIELDS)
+def test_recode_identity_mix_forwards_packets(n):
+    g = synth.choice(20, n)
+    coef = synth.coefficients(g, n, (6, 4), nonzero=False)
+    pay = synth.random_bytes(g, (6, 99))
+    c2, p2 = oracle.recode(n, coef, pay, np.eye(6, dtype=np.uint8))
+    assert np.array_equal(c2, coef) and np.array_equal(p2, pay)
+
+
+@pytest.mark.parametrize("n", FIELDS)
+def test_recoded_packets_decode_to_the_sources(n):
+    """Sources -> coded at the sender -> recoded at a relay -> decoded with the
+    composed coding vectors: the relay's vectors must describe its packets in
+    the original sources (a wrong composition fails the decode)."""
+    g = synth.choice(21, n)
+    N, L = 8, 300
+    src = synth.random_bytes(g, (N, L))
+    for attempt in range(20):
+        C = synth.coefficients(g, n, (N + 6, N), nonzero=False)
+        M = synth.coefficients(g, n, (N + 10, N + 6), nonzero=False)
+        c2, p2 = oracle.recode(n, C, oracle.encode(n, src, C), M)
+        if oracle.rank(n, c2) == N:
+            break
+    out, solved, rank, _ = oracle.decode(n, c2, p2)
+    assert rank == N and solved.all()
+    assert np.array_equal(out, src)
+
+
+@pytest.mark.parametrize("n", FIELDS)
+def test_recode_payload_is_encode_and_vectors_are_product(n):
+    g = synth.choice(22, n)
+    C = synth.coefficients(g, n, (5, 7), nonzero=False)
+    pay = synth.random_bytes(g, (5, 64))
+    M = synth.coefficients(g, n, (3, 5), nonzero=False)
+    c2, p2 = oracle.recode(n, C, pay, M)
+    assert np.array_equal(p2, oracle.encode(n, pay, M))
+    assert np.array_equal(c2, _matmul(n, M, C))
+
+
+def test_recode_gf2_is_xor_of_selected_rows():
+    """GF(2): a mix row selects packets; the new packet and vector are the
+    bitwise XOR of the selected ones (no field multiplication involved)."""
+    g = synth.choice(23)
+    C = synth.coefficients(g, 1, (9, 6), nonzero=False)
+    pay = synth.random_bytes(g, (9, 50))
+    M = synth.coefficients(g, 1, (4, 9), nonzero=False)
+    c2, p2 = oracle.recode(1, C, pay, M)
+    for k in range(4):
+        sel = np.nonzero(M[k])[0]
+        want_c = np.bitwise_xor.reduce(C[sel], axis=0) if sel.size else np.zeros(6, np.uint8)
+        want_p = np.bitwise_xor.reduce(pay[sel], axis=0) if sel.size else np.zeros(50, np.uint8)
+        assert np.array_equal(c2[k], want_c) and np.array_equal(p2[k], want_p)
