@@ -211,6 +211,45 @@ int gf_decode_noalloc(int field, int n_src, int n_recv, uint64_t len, const uint
                       uint8_t *out, int32_t *rank, int32_t *used, uint8_t *solved, gf_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Recoding at intermediate nodes                                      */
+/* ------------------------------------------------------------------ */
+
+/*
+ * A node of a coded network forwards linear combinations of the coded
+ * packets it has received (section II).  For one generation it holds n_in
+ * coded packets with their coding vectors and makes n_out new ones with
+ * fresh coefficients mix (n_out x n_in, one element per byte):
+ *   payload_out_k = sum_r mix[k][r] * payload_in_r     (Eq. 2)
+ *   coef_out_k    = sum_r mix[k][r] * coef_in_r        (the new packets'
+ *                   coding vectors with respect to the original sources)
+ *   coef_in      device, n_in x n_src, one element per byte
+ *   payload_in   device, n_in x len
+ *   mix          device, n_out x n_in
+ *   coef_out     device, n_out x n_src
+ *   payload_out  device, n_out x len
+ * Outputs must not overlap the inputs.
+ */
+typedef struct gf_recode {
+    int32_t field;
+    int32_t n_src;    /* N: length of the coding vectors */
+    int32_t n_in;     /* R: coded packets held */
+    int32_t n_out;    /* coded packets to make */
+    uint64_t len;
+    const uint8_t *coef_in;
+    const uint8_t *payload_in;
+    const uint8_t *mix;
+    uint8_t *coef_out;
+    uint8_t *payload_out;
+} gf_recode_t;
+
+/* gf_recode_batched: recode n_gens generations in one batched encode launch
+ * (payloads and coding vectors alike, as both are linear combinations with
+ * the same coefficients; a coding vector holds one element per byte, which
+ * the byte-packed field arithmetic multiplies exactly).  Errors: GF_EINVAL,
+ * GF_ENOMEM, GF_ECUDA. */
+int gf_recode_batched(const gf_recode_t *gens, int n_gens, gf_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Resident decoders: packets arrive over time (serving)               */
 /* ------------------------------------------------------------------ */
 

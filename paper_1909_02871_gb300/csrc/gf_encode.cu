@@ -474,3 +474,22 @@ extern "C" int gf_encode_validate(const gf_gen_t *gens, int n_gens, gf_stream_t 
     if (st == GF_OK && h) st = GF_EINVAL;
     return st;
 }
+
+// Recoding (section II: a node forwards combinations of what it received):
+// the payloads and the coding vectors are combined with the same fresh
+// coefficients, so each recoded generation is two encodes of one batch --
+// the coding vectors as n_in "packets" of n_src bytes (one element per byte,
+// upper words zero, which the packed arithmetic carries through exactly).
+extern "C" int gf_recode_batched(const gf_recode_t *gens, int n_gens, gf_stream_t stream)
+{
+    if (n_gens < 0 || (n_gens > 0 && !gens)) return GF_EINVAL;
+    std::vector<gf_gen_t> enc;
+    enc.reserve(2 * (size_t)n_gens);
+    for (int i = 0; i < n_gens; ++i) {
+        const gf_recode_t &r = gens[i];
+        if (r.n_src < 0 || r.n_in < 0 || r.n_out < 0) return GF_EINVAL;
+        enc.push_back(gf_gen_t{r.field, r.n_in, r.n_out, 0, r.len, r.payload_in, r.mix, r.payload_out});
+        enc.push_back(gf_gen_t{r.field, r.n_in, r.n_out, 0, (uint64_t)r.n_src, r.coef_in, r.mix, r.coef_out});
+    }
+    return encode_batched_impl(enc.data(), (int)enc.size(), GF_PATH_AUTO, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -35,6 +35,13 @@ class GfGen(ctypes.Structure):
                 ("coef", ctypes.c_void_p), ("out", ctypes.c_void_p)]
 
 
+class GfRecode(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_int32), ("n_src", ctypes.c_int32), ("n_in", ctypes.c_int32),
+                ("n_out", ctypes.c_int32), ("len", ctypes.c_uint64), ("coef_in", ctypes.c_void_p),
+                ("payload_in", ctypes.c_void_p), ("mix", ctypes.c_void_p), ("coef_out", ctypes.c_void_p),
+                ("payload_out", ctypes.c_void_p)]
+
+
 class GfDec(ctypes.Structure):
     _fields_ = [("field", ctypes.c_int32), ("n_src", ctypes.c_int32), ("n_recv", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("len", ctypes.c_uint64), ("coef", ctypes.c_void_p),
@@ -83,6 +90,7 @@ _SIGS = {
     "gf_dec_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p)]),
     "gf_dec_close": (ctypes.c_int, [ctypes.c_void_p]),
+    "gf_recode_batched": (ctypes.c_int, [ctypes.POINTER(GfRecode), ctypes.c_int, ctypes.c_void_p]),
     "gf_dec_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
@@ -193,6 +201,15 @@ def gf_encode_validate(gens, stream=None) -> int:
 def encode_status(gens, path: int = PATH_AUTO, stream=None) -> int:
     arr, n = gens if isinstance(gens, tuple) else make_gens(gens)
     return load().gf_encode_batched_ex(arr, n, path, _stream(stream))
+
+
+def gf_recode_batched(items, stream=None) -> None:
+    """items: iterable of (field, n_src, n_in, n_out, len, coef_in, payload_in, mix, coef_out, payload_out)."""
+    items = list(items)
+    arr = (GfRecode * max(1, len(items)))()
+    for i, (field, n_src, n_in, n_out, length, ci, pi, mix, co, po) in enumerate(items):
+        arr[i] = GfRecode(field, n_src, n_in, n_out, length, _ptr(ci), _ptr(pi), _ptr(mix), _ptr(co), _ptr(po))
+    _check(load().gf_recode_batched(arr, len(items), _stream(stream)), "gf_recode_batched")
 
 
 def gf_decode_batched(decs, stream=None) -> None:
