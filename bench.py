@@ -541,9 +541,10 @@ def run_recode(args, rank, world, local_rank):
     po = torch.empty((N_GENS, N_CODED, LEN), dtype=torch.uint8, device=dev)
     items = [(8, N_SRC, N_CODED, N_CODED, LEN, ci[i], pi[i], mx[i], co[i], po[i]) for i in range(N_GENS)]
     stream = torch.cuda.Stream(device=dev)
+    plan = gf.Plan.recode(items)  # descriptors uploaded once, like the uniform encode's plan
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            gf.gf_recode_batched(items, stream=stream)
+            plan.launch(stream)
     stream.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     rank_barrier()
@@ -552,7 +553,7 @@ def run_recode(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             ev[0].record(stream)
             for i in range(args.steps):
-                gf.gf_recode_batched(items, stream=stream)
+                plan.launch(stream)
                 ev[i + 1].record(stream)
         stream.synchronize()
     torch.cuda.synchronize()
@@ -570,7 +571,66 @@ def run_recode(args, rank, world, local_rank):
             "config": {"workload": "recode: 4096 generations, 64 coded packets of 1500 B held, 64 recoded packets "
                                    "and their coding vectors made per generation, GF(256)",
                        "l2": "inputs larger than L2"},
-            "clocks": clk.summary(), "round_trip_ok": ok, "gpu_launches": 1 * args.steps}
+            "clocks": clk.summary(), "round_trip_ok": ok, "gpu_launches": plan.kernel_count * args.steps}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_fig1(args, rank, world, local_rank):
+    """The paper's Fig. 1 workload on the GPU: generations of N = 16 packets,
+    K = 16 random combinations, packet size 128 B .. 64 KiB, each field.  One
+    batched encode per step over enough generations to fill the GPU (about
+    256 MB of coded output, at least 1024 generations); GB/s of coded output
+    (the paper's throughput) and the same per SM."""
+    import torch
+
+    from paper_1909_02871_gb300 import gf, synth
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    stream = torch.cuda.Stream(device=dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    points, launches = [], 0
+    rank_barrier()
+    with Clocks(local_rank) as clk:
+        for field in (1, 2, 4, 8):
+            for e in range(7, 17):
+                P = 1 << e
+                G = int(min(65536, max(1024, (256 << 20) // (16 * P))))
+                g = synth.choice(96, field, P)
+                src = torch.randint(0, 256, (G, 16, P), dtype=torch.uint8, device=dev)
+                coef = torch.from_numpy(synth.coefficients(g, field, (G, 16, 16), nonzero=True)).to(dev)
+                out = torch.empty((G, 16, P), dtype=torch.uint8, device=dev)
+                # the autotuner times the table tile shapes and the tensor-core path for this shape bucket
+                path, variant = gf.gf_autotune_encode(field, 16, 16, P, min(G, 2048), stream=stream)
+                plan = gf.Plan.encode([(field, 16, 16, P, src[i], coef[i], out[i]) for i in range(G)])
+                with torch.cuda.stream(stream):
+                    for _ in range(3):
+                        plan.launch(stream)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(args.steps):
+                        plan.launch(stream)
+                    e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                gbs = G * 16 * P / (ms / 1e3) / 1e9
+                points.append({"field": field, "packet_bytes": P, "generations": G, "ms": ms, "GBps_coded": gbs,
+                               "GBps_coded_per_SM": gbs / n_sm,
+                               "path": {1: "table", 2: "bitsliced"}.get(path, path), "table_variant": variant})
+                launches += plan.kernel_count * args.steps
+                plan.close()
+                del src, coef, out
+    torch.cuda.empty_cache()
+    line = {"metric": "N=16 encode GB/s of coded output vs packet size (Fig. 1 workload)",
+            "value": statistics.median(p["GBps_coded"] for p in points), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": 3, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "generations of N=16, K=16 random combinations, packet 128 B..64 KiB, GF(2), "
+                                   "GF(4), GF(16), GF(256); >= 1024 generations per point (about 256 MB out)",
+                       "value_is": "median over the 40 points"},
+            "points": points, "clocks": clk.summary(), "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -712,7 +772,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gf", "reference"], default="gf")
-    ap.add_argument("--workload", choices=["uniform", "uneven", "serve", "region", "single", "recode"], default="uniform")
+    ap.add_argument("--workload", choices=["uniform", "uneven", "serve", "region", "single", "recode", "fig1"], default="uniform")
     ap.add_argument("--gens", type=int, default=2048, help="generations of the uneven workload")
     ap.add_argument("--requests", type=int, default=600, help="requests of the serving workload")
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
@@ -748,6 +808,8 @@ def main():
         run_single(args, rank, world, local_rank)
     elif args.workload == "recode":
         run_recode(args, rank, world, local_rank)
+    elif args.workload == "fig1":
+        run_fig1(args, rank, world, local_rank)
     else:
         run_gf(args, rank, world, local_rank)
     if world > 1 and args.impl == "gf":

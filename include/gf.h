@@ -329,6 +329,9 @@ int gf_encode_plan_create(const gf_gen_t *gens, int n_gens, int path, gf_plan_t 
 /* gf_decode_plan_create: the same for a decode batch. */
 int gf_decode_plan_create(const gf_dec_t *gens, int n_gens, gf_plan_t **plan);
 
+/* A plan of gf_recode_batched's work for gens (same arguments). */
+int gf_recode_plan_create(const gf_recode_t *gens, int n_gens, gf_plan_t **plan);
+
 /* gf_plan_launch: enqueues the plan's kernels on `stream` (no allocation, no
  * host-device copy: safe inside stream capture). */
 int gf_plan_launch(gf_plan_t *plan, gf_stream_t stream);

@@ -343,10 +343,17 @@ int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBa
     EncodeBatch table, bits;
     table.kind = GF_PATH_TABLE;
     bits.kind = GF_PATH_BITSLICED;
+    // A batch of fewer generations than about two per SM cannot fill the GPU
+    // through the table path's per-generation tiles; the tensor-core path
+    // spreads each generation's column tiles over CTAs, so AUTO takes it.
+    const bool small_batch = gens.size() < (size_t)(2 * sm_count());
     for (const EncGen &g0 : gens) {
         EncGen g = g0;
         int p = path;
-        if (p == GF_PATH_AUTO) p = choose_path(g.field, g.n_src, g.n_coded, g.len);
+        if (p == GF_PATH_AUTO)
+            p = small_batch && bitsliced_available() && bitsliced_supports(g)
+                    ? GF_PATH_BITSLICED
+                    : choose_path(g.field, g.n_src, g.n_coded, g.len);
         if (p == GF_PATH_BITSLICED) {
             if (!bitsliced_available()) {
                 if (path == GF_PATH_BITSLICED) return GF_ENOTSUP;

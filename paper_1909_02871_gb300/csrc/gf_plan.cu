@@ -69,9 +69,6 @@ int choose_table_variant(int field, int n_src, int n_coded, unsigned long long l
     return n_coded <= 8 ? 3 : 0;          // 512-byte column tiles
 }
 
-constexpr int kBitslicedMinSrc = 16, kBitslicedMinCoded = 16;
-constexpr unsigned long long kBitslicedMinLen = 256;
-
 int choose_path(int field, int n_src, int n_coded, unsigned long long len)
 {
     {
@@ -79,12 +76,16 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len)
         auto it = g_tune.find(tune_key(field, n_src, n_coded, len));
         if (it != g_tune.end()) return it->second.path;
     }
-    // every field goes to the tensor cores once a 128-byte x 32-packet x
-    // 64-source pass holds enough work to beat the table path's integer
-    // operations per word and coefficient
-    if (bitsliced_available() && n_src >= kBitslicedMinSrc && n_coded >= kBitslicedMinCoded &&
-        len >= kBitslicedMinLen)
-        return GF_PATH_BITSLICED;
+    if (!bitsliced_available() || n_src <= 0 || n_coded <= 0 || len == 0) return GF_PATH_TABLE;
+    // Cost model in SM clocks per generation, from GB300 measurements: a
+    // tensor-core D pass (128 bytes x 32 coded packets x up to 64 sources)
+    // costs about 2700 clocks however full it is (synchronisation, not MMA
+    // work, dominates); the table path costs about 53 clocks per source for
+    // every 128-byte x 8-packet tile (GF(2), a plain XOR, about 0.77 of that).
+    const double tiles = std::ceil((double)len / 128.0);
+    const double bits = std::ceil(n_src / 64.0) * tiles * std::ceil(n_coded / 32.0) * 2700.0;
+    const double table = tiles * std::ceil(n_coded / 8.0) * 53.0 * n_src * (field == 1 ? 0.77 : 1.0);
+    if (bits < table) return GF_PATH_BITSLICED;
     return GF_PATH_TABLE;
 }
 
@@ -158,6 +159,23 @@ extern "C" int gf_encode_plan_create(const gf_gen_t *gens, int n_gens, int path,
     }
     *plan = p;
     return GF_OK;
+}
+
+// A recode plan is the encode plan of its payload and coding-vector encodes
+// (gf_recode_batched's decomposition).
+extern "C" int gf_recode_plan_create(const gf_recode_t *gens, int n_gens, gf_plan_t **plan)
+{
+    if (!plan || n_gens < 0 || (n_gens > 0 && !gens)) return GF_EINVAL;
+    *plan = nullptr;
+    std::vector<gf_gen_t> enc;
+    enc.reserve(2 * (size_t)n_gens);
+    for (int i = 0; i < n_gens; ++i) {
+        const gf_recode_t &r = gens[i];
+        if (r.n_src < 0 || r.n_in < 0 || r.n_out < 0) return GF_EINVAL;
+        enc.push_back(gf_gen_t{r.field, r.n_in, r.n_out, 0, r.len, r.payload_in, r.mix, r.payload_out});
+        enc.push_back(gf_gen_t{r.field, r.n_in, r.n_out, 0, (uint64_t)r.n_src, r.coef_in, r.mix, r.coef_out});
+    }
+    return gf_encode_plan_create(enc.data(), (int)enc.size(), GF_PATH_AUTO, plan);
 }
 
 extern "C" int gf_decode_plan_create(const gf_dec_t *gens, int n_gens, gf_plan_t **plan)

@@ -91,6 +91,8 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p)]),
     "gf_dec_close": (ctypes.c_int, [ctypes.c_void_p]),
     "gf_recode_batched": (ctypes.c_int, [ctypes.POINTER(GfRecode), ctypes.c_int, ctypes.c_void_p]),
+    "gf_recode_plan_create": (ctypes.c_int, [ctypes.POINTER(GfRecode), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
     "gf_dec_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
@@ -203,13 +205,18 @@ def encode_status(gens, path: int = PATH_AUTO, stream=None) -> int:
     return load().gf_encode_batched_ex(arr, n, path, _stream(stream))
 
 
-def gf_recode_batched(items, stream=None) -> None:
+def make_recodes(items):
     """items: iterable of (field, n_src, n_in, n_out, len, coef_in, payload_in, mix, coef_out, payload_out)."""
     items = list(items)
     arr = (GfRecode * max(1, len(items)))()
     for i, (field, n_src, n_in, n_out, length, ci, pi, mix, co, po) in enumerate(items):
         arr[i] = GfRecode(field, n_src, n_in, n_out, length, _ptr(ci), _ptr(pi), _ptr(mix), _ptr(co), _ptr(po))
-    _check(load().gf_recode_batched(arr, len(items), _stream(stream)), "gf_recode_batched")
+    return arr, len(items)
+
+
+def gf_recode_batched(items, stream=None) -> None:
+    arr, n = items if isinstance(items, tuple) else make_recodes(items)
+    _check(load().gf_recode_batched(arr, n, _stream(stream)), "gf_recode_batched")
 
 
 def gf_decode_batched(decs, stream=None) -> None:
@@ -298,6 +305,13 @@ class Plan:
         arr, n = gens if isinstance(gens, tuple) else make_gens(gens)
         h = ctypes.c_void_p()
         _check(load().gf_encode_plan_create(arr, n, path, ctypes.byref(h)), "gf_encode_plan_create")
+        return cls(h.value, arr)
+
+    @classmethod
+    def recode(cls, items) -> "Plan":
+        arr, n = items if isinstance(items, tuple) else make_recodes(items)
+        h = ctypes.c_void_p()
+        _check(load().gf_recode_plan_create(arr, n, ctypes.byref(h)), "gf_recode_plan_create")
         return cls(h.value, arr)
 
     @classmethod

@@ -77,3 +77,20 @@ def test_recoded_packets_decode_on_the_gpu(field):
     c2h = to_host(c2).reshape(N + 12, N)
     assert int(rank.item()) == oracle.rank(field, c2h) == N
     assert np.array_equal(to_host(out).reshape(N, L), src)
+
+
+def test_recode_plan_equals_call():
+    g = synth.choice(93)
+    N, R, K2, L = 32, 40, 36, 1000
+    ci = synth.coefficients(g, 8, (R, N), nonzero=False)
+    pi = synth.random_bytes(g, (R, L))
+    mix = synth.coefficients(g, 8, (K2, R), nonzero=False)
+    d_ci, d_pi, d_mix = to_dev(ci.reshape(-1)), to_dev(pi.reshape(-1)), to_dev(mix.reshape(-1))
+    co = torch.zeros(K2 * N, dtype=torch.uint8, device=dev())
+    po = torch.zeros(K2 * L, dtype=torch.uint8, device=dev())
+    plan = gf.Plan.recode([(8, N, R, K2, L, d_ci, d_pi, d_mix, co, po)])
+    plan.launch()
+    torch.cuda.synchronize()
+    wc, wp = oracle.recode(8, ci, pi, mix)
+    assert np.array_equal(to_host(co).reshape(K2, N), wc) and np.array_equal(to_host(po).reshape(K2, L), wp)
+    plan.close()
