@@ -60,7 +60,8 @@ size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem)
 // f_t * rows[t][same word], u < U; then one atomicXor per word and warp
 template <int U>
 __device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *rows, const uint8_t *fsnap,
-                                               const DecMap *tab, int rank, int nw, int j0, int warp, int lane)
+                                               const DecMap *tab, int rank, int nw, int nw_r, int j0, int warp,
+                                               int lane)
 {
     uint32_t acc[U];
 #pragma unroll
@@ -72,11 +73,11 @@ __device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *ro
         const uint32_t *row = rows + (size_t)t * nw + j0 + lane;
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (j0 + lane + 32 * u < nw) acc[u] ^= apply_word(m, row[32 * u]);
+            if (j0 + lane + 32 * u < nw_r) acc[u] ^= apply_word(m, row[32 * u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-        if (j0 + lane + 32 * u < nw && acc[u]) atomicXor(&cur[j0 + lane + 32 * u], acc[u]);
+        if (j0 + lane + 32 * u < nw_r && acc[u]) atomicXor(&cur[j0 + lane + 32 * u], acc[u]);
 }
 
 __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *__restrict__ gens)
@@ -157,14 +158,18 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         //    the stored rows t = w (mod the warp count); each lane accumulates its word
         //    columns (up to four, as many as the row is wide, in independent
         //    registers) and one atomicXor per word and warp combines the warps.
+        // Rows received so far carry transform entries only in columns N .. N+r
+        // (each row starts as its own unit vector), so every word past
+        // column N+r is zero in the stored rows and in the arriving row:
+        // the row operations stop at word nw_r.
+        const int nw_r = min(nw, (N + r + 1 + 3) / 4);
         if (rank > 0) {
-            const int wpl = (nw + 31) / 32;  // words per lane
-            for (int j0 = 0; j0 < nw; j0 += 128) {
-                const int left = min(4, (nw - j0 + 31) / 32);
-                if (wpl >= 4 && left == 4) eliminate_rows<4>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
-                else if (left == 3) eliminate_rows<3>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
-                else if (left == 2) eliminate_rows<2>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
-                else eliminate_rows<1>(cur, rows, fsnap, tab, rank, nw, j0, warp, lane);
+            for (int j0 = 0; j0 < nw_r; j0 += 128) {
+                const int left = min(4, (nw_r - j0 + 31) / 32);
+                if (left == 4) eliminate_rows<4>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
+                else if (left == 3) eliminate_rows<3>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
+                else if (left == 2) eliminate_rows<2>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
+                else eliminate_rows<1>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
             }
         }
         __syncthreads();
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         // 5. normalise
         {
             const ByteMap m = tab[s_inv].m;
-            for (int j = tid; j < nw; j += blockDim.x) cur[j] = apply_word(m, cur[j]);
+            for (int j = tid; j < nw_r; j += blockDim.x) cur[j] = apply_word(m, cur[j]);
         }
         // 6. column `piv` of every stored row
         for (int s = tid; s < rank; s += blockDim.x)
@@ -208,10 +213,10 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         //    A thread owns a word column j (its prmt selectors computed once)
         //    and walks a share of the stored rows.
         {
-            const int per = max(1, kDecThreads / max(nw, 1));  // threads per column
+            const int per = max(1, kDecThreads / max(nw_r, 1));  // threads per column
             const int cols = kDecThreads / per;
             const int j_start = tid % cols, part = tid / cols;
-            for (int j = j_start; j < nw && part < per; j += cols) {
+            for (int j = j_start; j < nw_r && part < per; j += cols) {
                 const uint32_t cw = cur[j];
                 const Sel sel = make_sel(cw);
                 for (int s = part; s < rank; s += per) {
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
                 }
                 if (part == 0) rows[(size_t)rank * nw + j] = cw;
             }
+            for (int j = nw_r + tid; j < nw; j += blockDim.x) rows[(size_t)rank * nw + j] = 0u;
         }
         __syncthreads();
         if (tid == 0) {
