@@ -56,28 +56,31 @@ size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem)
     return b;
 }
 
-// cur[j0 + lane + 32u] ^= sum over stored rows t = warp (mod number of warps) of
-// f_t * rows[t][same word], u < U; then one atomicXor per word and warp
-template <int U>
+// cur[j0 + 4 lane .. +3] ^= sum over stored rows t = warp (mod the warp count)
+// of f_t * rows[t][same words]: one 16-byte shared load per row and lane, the
+// row's byte map loaded once for four words; then one atomicXor per word and
+// warp combines the warps (nw, j0 multiples of 4)
 __device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *rows, const uint8_t *fsnap,
                                                const DecMap *tab, int rank, int nw, int nw_r, int j0, int warp,
                                                int lane)
 {
-    uint32_t acc[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = 0u;
+    const int j = j0 + 4 * lane;
+    if (j >= nw_r) return;  // lanes past the live words have nothing to add (no warp-wide operations below)
+    uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
     for (int t = warp; t < rank; t += kDecThreads / 32) {
         const uint32_t f = fsnap[t];
         if (!f) continue;
         const ByteMap m = tab[f].m;
-        const uint32_t *row = rows + (size_t)t * nw + j0 + lane;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (j0 + lane + 32 * u < nw_r) acc[u] ^= apply_word(m, row[32 * u]);
+        const uint4 w = *reinterpret_cast<const uint4 *>(rows + (size_t)t * nw + j);
+        a0 ^= apply_word(m, w.x);
+        a1 ^= apply_word(m, w.y);
+        a2 ^= apply_word(m, w.z);
+        a3 ^= apply_word(m, w.w);
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-        if (j0 + lane + 32 * u < nw_r && acc[u]) atomicXor(&cur[j0 + lane + 32 * u], acc[u]);
+    if (a0) atomicXor(&cur[j], a0);
+    if (a1) atomicXor(&cur[j + 1], a1);
+    if (a2) atomicXor(&cur[j + 2], a2);
+    if (a3) atomicXor(&cur[j + 3], a3);
 }
 
 __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *__restrict__ gens)
@@ -122,26 +125,24 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     }
     __syncthreads();
 
-    // coefficient words of the next arriving row, prefetched a row ahead
-    // (a thread owns coefficient word tid; N <= 4 * kDecThreads)
-    auto fetch = [&](int rr) -> uint32_t {
-        uint32_t v = 0;
-        if (rr < R && 4 * tid < N) {
-            const uint8_t *crow = g.coef + (size_t)rr * N;
+    // coefficient bytes of the next arriving row, prefetched a row ahead: the
+    // four loads are issued here and only combined into a word when the row
+    // is used, a whole row step later, so their latency is hidden (a thread
+    // owns coefficient word tid; N <= 4 * kDecThreads)
+    uint32_t nb[4];
+    auto fetch = [&](int rr) {
 #pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (4 * tid + b < N) v |= (uint32_t)crow[4 * tid + b] << (8 * b);
-        }
-        return v;
+        for (int b = 0; b < 4; ++b)
+            nb[b] = (rr < R && 4 * tid + b < N) ? (uint32_t)__ldg(g.coef + (size_t)rr * N + 4 * tid + b) : 0u;
     };
-    uint32_t next = fetch(0);
+    fetch(0);
     int r = 0;
     for (; r < R; ++r) {
         const int rank = s_rank;
         if (rank >= N) break;
         // 1. the arriving row: [coef | unit vector e_r]
-        const uint32_t mine = next;
-        next = fetch(r + 1);
+        const uint32_t mine = nb[0] | (nb[1] << 8) | (nb[2] << 16) | (nb[3] << 24);
+        fetch(r + 1);
         for (int j = tid; j < nw; j += blockDim.x) {
             uint32_t v = j == tid ? mine : 0u;
 #pragma unroll
@@ -162,16 +163,9 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         // (each row starts as its own unit vector), so every word past
         // column N+r is zero in the stored rows and in the arriving row:
         // the row operations stop at word nw_r.
-        const int nw_r = min(nw, (N + r + 1 + 3) / 4);
-        if (rank > 0) {
-            for (int j0 = 0; j0 < nw_r; j0 += 128) {
-                const int left = min(4, (nw_r - j0 + 31) / 32);
-                if (left == 4) eliminate_rows<4>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
-                else if (left == 3) eliminate_rows<3>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
-                else if (left == 2) eliminate_rows<2>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
-                else eliminate_rows<1>(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
-            }
-        }
+        const int nw_r = min(nw, (N + r + 1 + 15) / 16 * 4);  // whole 16-byte groups
+        if (rank > 0)
+            for (int j0 = 0; j0 < nw_r; j0 += 128) eliminate_rows(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
         __syncthreads();
         // 4. pivot: first nonzero coefficient (warp 0, ballot over words)
         if (warp == 0) {
@@ -213,17 +207,27 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         //    A thread owns a word column j (its prmt selectors computed once)
         //    and walks a share of the stored rows.
         {
-            const int per = max(1, kDecThreads / max(nw_r, 1));  // threads per column
-            const int cols = kDecThreads / per;
-            const int j_start = tid % cols, part = tid / cols;
-            for (int j = j_start; j < nw_r && part < per; j += cols) {
-                const uint32_t cw = cur[j];
-                const Sel sel = make_sel(cw);
+            const int ng = nw_r / 4;                               // 16-byte word groups
+            const int per = max(1, kDecThreads / max(ng, 1));      // threads per group
+            const int groups = kDecThreads / per;
+            const int g_start = tid % groups, part = tid / groups;
+            for (int gq = g_start; gq < ng && part < per; gq += groups) {
+                const int j = 4 * gq;
+                const uint4 cw = *reinterpret_cast<const uint4 *>(cur + j);
+                const Sel s0 = make_sel(cw.x), s1 = make_sel(cw.y), s2 = make_sel(cw.z), s3 = make_sel(cw.w);
                 for (int s = part; s < rank; s += per) {
                     const uint32_t f = gsnap[s];
-                    if (f) rows[(size_t)s * nw + j] ^= apply(tab[f].m, sel);
+                    if (!f) continue;
+                    const ByteMap m = tab[f].m;
+                    uint4 *rw = reinterpret_cast<uint4 *>(rows + (size_t)s * nw + j);
+                    uint4 w = *rw;
+                    w.x ^= apply(m, s0);
+                    w.y ^= apply(m, s1);
+                    w.z ^= apply(m, s2);
+                    w.w ^= apply(m, s3);
+                    *rw = w;
                 }
-                if (part == 0) rows[(size_t)rank * nw + j] = cw;
+                if (part == 0) *reinterpret_cast<uint4 *>(rows + (size_t)rank * nw + j) = cw;
             }
             for (int j = nw_r + tid; j < nw; j += blockDim.x) rows[(size_t)rank * nw + j] = 0u;
         }
