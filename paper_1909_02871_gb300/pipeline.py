@@ -154,3 +154,79 @@ def decoded(work: UnevenWork, i: int) -> np.ndarray:
     g = work.batch.gens[i]
     off = work.dev["_src_off"][i]
     return work.dev["out"][off:off + g.src.size].cpu().numpy().reshape(g.n_src, g.length)
+
+
+class HostEncoder:
+    """Batched encode of generations whose sources, coding matrices and coded
+    packets live in pinned host memory: every step uploads the inputs,
+    encodes and downloads the coded packets.  The batch is cut into chunks
+    (one plan each) run on three streams -- uploads, encodes, downloads -- so
+    chunk k+1's upload, chunk k's encode and chunk k-1's download overlap;
+    events order each chunk's three stages and keep a step from overwriting a
+    chunk's device buffers before the previous step is done with them.
+
+    src_h (G x N x L), coef_h (G x K x N), out_h (G x K x L): pinned uint8
+    host tensors; src_d, coef_d, out_d: device tensors of the same shapes."""
+
+    def __init__(self, field: int, src_h, coef_h, out_h, src_d, coef_d, out_d, chunks: int = 8,
+                 path: int = gf.PATH_AUTO, copy_streams: int = 1):
+        import torch
+        self.torch = torch
+        G, N, L = src_h.shape
+        K = coef_h.shape[1]
+        self.h = (src_h, coef_h, out_h)
+        self.d = (src_d, coef_d, out_d)
+        bounds = np.linspace(0, G, min(chunks, G) + 1).astype(int)
+        self.ranges = [(int(a), int(b)) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        self.plans = [gf.Plan.encode([(field, N, K, L, src_d[i], coef_d[i], out_d[i]) for i in range(a, b)],
+                                     path=path) for a, b in self.ranges]
+        dev = src_d.device
+        # several upload and download streams, used in turn by the chunks, so
+        # that more than one copy engine per direction is busy
+        self.ups = [torch.cuda.Stream(device=dev) for _ in range(copy_streams)]
+        self.downs = [torch.cuda.Stream(device=dev) for _ in range(copy_streams)]
+        self.enc = torch.cuda.Stream(device=dev)
+        self.up, self.down = self.ups[0], self.downs[-1]
+        n = len(self.ranges)
+        self.ev_up = [torch.cuda.Event() for _ in range(n)]
+        self.ev_enc = [torch.cuda.Event() for _ in range(n)]
+        self.ev_down = [torch.cuda.Event() for _ in range(n)]
+        self.first = True
+
+    @property
+    def kernel_count(self) -> int:
+        return sum(p.kernel_count for p in self.plans)
+
+    def step(self) -> None:
+        """Enqueue one step (returns without waiting)."""
+        src_h, coef_h, out_h = self.h
+        src_d, coef_d, out_d = self.d
+        for c, (a, b) in enumerate(self.ranges):
+            up = self.ups[c % len(self.ups)]
+            down = self.downs[c % len(self.downs)]
+            with self.torch.cuda.stream(up):
+                if not self.first:
+                    up.wait_event(self.ev_enc[c])  # the previous encode of this chunk has read its inputs
+                src_d[a:b].copy_(src_h[a:b], non_blocking=True)
+                coef_d[a:b].copy_(coef_h[a:b], non_blocking=True)
+                self.ev_up[c].record(up)
+            with self.torch.cuda.stream(self.enc):
+                self.enc.wait_event(self.ev_up[c])
+                if not self.first:
+                    self.enc.wait_event(self.ev_down[c])  # the previous download of this chunk is done
+                self.plans[c].launch(self.enc)
+                self.ev_enc[c].record(self.enc)
+            with self.torch.cuda.stream(down):
+                down.wait_event(self.ev_enc[c])
+                out_h[a:b].copy_(out_d[a:b], non_blocking=True)
+                self.ev_down[c].record(down)
+        self.first = False
+
+    def synchronize(self) -> None:
+        for d in self.downs:
+            d.synchronize()
+
+    def close(self) -> None:
+        for p in self.plans:
+            p.close()
+        self.plans = []

@@ -187,3 +187,29 @@ def test_full_uniform_batch_sampled():
         torch.cuda.synchronize()
         for i in (0, 1, 2047, 4095):
             assert np.array_equal(out[i].cpu().numpy(), oracle.encode(8, b.src[i], b.coef[i])), (path, i)
+
+
+def test_host_encoder_pipelined_steps():
+    """pipeline.HostEncoder: host-resident batch in chunks on three streams;
+    two steps in a row (the second reusing the device buffers while the
+    first's downloads may still run) give the oracle's coded packets."""
+    from paper_1909_02871_gb300 import pipeline
+    dev()
+    G, N, K, L = 40, 16, 24, 700
+    g = synth.choice(97)
+    src = synth.random_bytes(g, (G, N, L))
+    coef = synth.coefficients(g, 8, (G, K, N), nonzero=False)
+    src_h = torch.from_numpy(src).pin_memory()
+    coef_h = torch.from_numpy(coef).pin_memory()
+    out_h = torch.zeros((G, K, L), dtype=torch.uint8).pin_memory()
+    src_d = torch.empty((G, N, L), dtype=torch.uint8, device=dev())
+    coef_d = torch.empty((G, K, N), dtype=torch.uint8, device=dev())
+    out_d = torch.empty((G, K, L), dtype=torch.uint8, device=dev())
+    enc = pipeline.HostEncoder(8, src_h, coef_h, out_h, src_d, coef_d, out_d, chunks=5)
+    enc.step()
+    enc.step()
+    enc.synchronize()
+    got = out_h.numpy()
+    for i in range(G):
+        assert np.array_equal(got[i], oracle.encode(8, src[i], coef[i])), i
+    enc.close()
