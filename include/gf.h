@@ -381,6 +381,15 @@ int gf_autotune_load(const char *path);
  * error word: GF_OK, or GF_ETIMEOUT if a bounded wait inside a kernel gave up. */
 int gf_device_status(void);
 
+/* Self-test of the device-side bounded waits (the paper has no counterpart):
+ * enqueues a one-warp kernel that waits on an mbarrier nothing will arrive
+ * at -- with abort_first != 0, with the CTA's abort flag already set -- using
+ * the same bounded wait as the tensor-core encode.  The wait gives up (after
+ * its 1 s limit, or at once when aborting), the kernel records GF_ETIMEOUT in
+ * the status word that gf_device_status reports and returns; nothing hangs
+ * or faults and the context stays usable.  Errors: GF_ENOMEM, GF_ECUDA. */
+int gf_selftest_wait(int abort_first, gf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len);
 
 // Whether the bit-sliced (tcgen05) path can run on the current device.
 bool bitsliced_available();
+// Launch the bounded-wait self-test (gf_selftest_wait).
+int launch_wait_selftest(int abort_first, cudaStream_t stream);
 
 // Whether a generation fits the bit-sliced kernel (GF(256), 1 <= N <= 128,
 // K >= 1, len >= 1); others of a bit-sliced batch run on the table path.

@@ -819,7 +819,32 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     }
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// will ever arrive at (or, with abort_first, with the abort flag already
+// set); the wait must give up, the kernel records GF_ETIMEOUT in the status
+// word and returns.
+__global__ void wait_selftest_kernel(int abort_first, int *status)
+{
+    __shared__ unsigned long long bar;
+    __shared__ int abort;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort = abort_first ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, &abort)) atomicExch(status, GF_ETIMEOUT);
+}
+
 }  // namespace tc
+
+int launch_wait_selftest(int abort_first, cudaStream_t stream)
+{
+    int *status = device_status_word();
+    if (!status) return GF_ENOMEM;
+    tc::wait_selftest_kernel<<<1, 32, 0, stream>>>(abort_first, status);
+    return cuda_status(cudaGetLastError());
+}
 
 bool bitsliced_available()
 {

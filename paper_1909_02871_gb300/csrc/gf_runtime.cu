@@ -7,6 +7,7 @@
 #include <utility>
 
 #include "gf_internal.cuh"
+#include "gf_encode.h"
 #include "gf_runtime.h"
 
 namespace gf {
@@ -160,4 +161,9 @@ extern "C" int gf_device_status(void)
     if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GF_ECUDA;
     if (cudaMemset(w, 0, sizeof(int)) != cudaSuccess) return GF_ECUDA;
     return v;
+}
+
+extern "C" int gf_selftest_wait(int abort_first, gf_stream_t stream)
+{
+    return gf::launch_wait_selftest(abort_first, reinterpret_cast<cudaStream_t>(stream));
 }

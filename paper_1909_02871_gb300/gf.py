@@ -82,6 +82,7 @@ _SIGS = {
     "gf_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "gf_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "gf_device_status": (ctypes.c_int, []),
+    "gf_selftest_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p]),
     "gf_dec_open": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_void_p)]),
     "gf_dec_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
