@@ -666,9 +666,9 @@ def run_region_sweep(args, rank, world, local_rank):
     crng = np.random.default_rng(1909)
     rank_barrier()
     with Clocks(local_rank) as clk, torch.cuda.stream(stream):
-        for field in (1, 2, 4, 8):
+        for field in args.region_fields:
             for op, fn, per in (("madd", gf.gf_region_madd, 3), ("mul", gf.gf_region_mul, 2)):
-                for e in range(10, 31):
+                for e in range(args.region_min_log, 31):
                     n = 1 << e
                     c = int(crng.integers(1, 1 << field)) if field > 1 else 1
                     for _ in range(3):
@@ -784,6 +784,8 @@ def main():
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--region-min-log", type=int, default=10, help="region sweep: smallest size 2^k bytes")
+    ap.add_argument("--region-fields", type=int, nargs="+", default=[1, 2, 4, 8], help="region sweep: fields")
     ap.add_argument("--uniform-gens", type=int, default=None,
                     help="generations of the uniform workload (smaller cases for profiler captures; "
                          "the reported workload is the 4096-generation batch only without it)")
