@@ -38,11 +38,11 @@
 // each half of its B as soon as the previous item's last pass over that half
 // is done; 8 producer warps stage their source rows in shared memory with
 // cp.async two tiles ahead and fill A (double-buffered in TMEM, via a 1 KB
-// table of pre-spread words); 1 thread issues the MMAs; 16 epilogue warps
-// drain D.  Handshakes arrive once per warp (after __syncwarp).  A role of
-// several warps waits through one elected thread that polls the mbarrier
-// while the others are parked on a named barrier, which also hands every
-// warp the same outcome.  Every mbarrier wait is bounded by the global
+// table of pre-spread words); 1 warp issues the MMAs (lane 0, the warp
+// converged); 16 epilogue warps drain D.  Handshakes arrive once per warp
+// (after __syncwarp).  A role of several warps waits through one polling
+// warp while the others are parked on a named barrier, which also hands
+// every warp the same outcome.  Every mbarrier wait is bounded by the global
 // timer; a wait that gives up records GF_ETIMEOUT in the library's device
 // status word, the CTA drains its MMAs (bounded), frees TMEM and exits.
 #include <cuda_runtime.h>
@@ -171,15 +171,23 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool pred)
     return r != 0;
 }
 
-// Wait of a whole role: one thread polls the mbarrier (bounded), the role's
-// other warps block on named barrier `id` (no issue slots while blocked) and
-// all of them adopt the outcome.  Returns false if the wait gave up.
-__device__ __forceinline__ bool role_wait(unsigned long long *bar, uint32_t parity, volatile int *abort, bool poller,
-                                          int id, int count)
+// Wait of a whole role: one warp polls the mbarrier (bounded; all its lanes,
+// so that the warp stays converged), the role's other warps block on named
+// barrier `id` (no issue slots while blocked) and all of them adopt the
+// outcome.  Returns false if the wait gave up.
+__device__ __forceinline__ bool role_wait(unsigned long long *bar, uint32_t parity, volatile int *abort,
+                                          bool poll_warp, int id, int count)
 {
     bool fail = false;
-    if (poller) fail = !mbar_wait(bar, parity, abort);
+    if (poll_warp) fail = __any_sync(0xffffffffu, !mbar_wait(bar, parity, abort));
     return !bar_or(id, count, fail);
+}
+
+// Wait of the MMA warp: every lane polls (bounded), the first test inline,
+// and the warp adopts one outcome.
+__device__ __forceinline__ bool warp_wait(unsigned long long *bar, uint32_t parity, volatile int *abort)
+{
+    return __all_sync(0xffffffffu, mbar_try(bar, parity) || mbar_wait(bar, parity, abort));
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -564,7 +572,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int pos = quarter * 32 + lane;   // byte position within the column tile
         const int ibase = part * kSrcPerProducer;
         unsigned char *stage = staging + warp * (kStages * kStageBytes);
-        const bool poller = tid == 0;
+        const bool poller = warp == 0;
         uint32_t fills = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
@@ -652,7 +660,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         const int quarter = warp & 3;
         const int oct = (warp - kProducerWarps) >> 2;   // 8-packet group of the item: 0..3
         const int pos = quarter * 32 + lane;
-        const bool poller = tid == kProducerWarps * 32;
+        const bool poller = warp == kProducerWarps;
         uint32_t tiles = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
@@ -720,14 +728,20 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             }
             if (!ok) break;
         }
-    } else if (lane == 0) {
-        // ---------------- MMA issuer (warp kMmaWarp, one thread) ----------------
+    } else {
+        // ---------------- MMA issuer (warp kMmaWarp; lane 0 issues) ----------------
+        // The whole warp runs the loop and waits together (a lone looping lane whose
+        // warp-mates sit at the final __syncthreads issues markedly slower).
         uint32_t fills = 0, tiles = 0;
         uint32_t bused0 = 0, bused1 = 0;  // fills of each B half consumed so far
+        // A buffer whose last pass was the previous pass: released by a plain arrival once
+        // the next pass's d_empty wait shows that the epilogue has read that pass's D (so
+        // its MMAs are complete); a tcgen05.commit with MMAs in flight stalls this warp
+        int release_a = -1;
         const uint64_t bias_desc = b_desc(smem_u32(bias_b));
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
-            if (!mbar_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
+            if (!warp_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
                 ctl->abort = 1;
                 break;
             }
@@ -736,7 +750,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int k0i = ctl->ring_k0[e];
             // column tiles of this item
             const int ncols = kColSplit ? ctl->ring_c1[e] - ctl->ring_c0[e] : (int)((g.len + kColTile - 1) / kColTile);
-            mbar_arrive(&ctl->info_empty[e]);
+            if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
@@ -745,7 +759,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 const int kc = v / ncols, ct = v - kc * ncols;  // 64-source chunk, column tile
                 const int ksteps = (min(kMaxSrc, g.n_src - kc * kMaxSrc) + 7) / 8;  // 8 sources per MMA
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
-                if (!mbar_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
+                if (!warp_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -753,36 +767,43 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 // the A tile serves both halves of the item: one D pass per 32 coded packets (each
                 // source chunk's B halves are built anew, so they are waited for at its first tile)
                 for (int h = 0; h < nh; ++h) {
-                    if (ct == 0 && !mbar_wait(&ctl->b_full[h], (h ? bused1 : bused0) & 1u, abort_flag)) {
+                    if (ct == 0 && !warp_wait(&ctl->b_full[h], (h ? bused1 : bused0) & 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    if (!mbar_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
+                    if (!warp_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
                         ok = false;
                         break;
+                    }
+                    if (release_a >= 0) {
+                        if (lane == 0) mbar_arrive(&ctl->a_empty[release_a]);
+                        release_a = -1;
                     }
                     tc_fence_after();
-                    // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field:
-                    // B lies below 256 KB of shared memory)
-                    const uint64_t bdesc0 = b_desc(smem_u32(Bs + h * kBBytes));
-                    const uint32_t dt = tmem + kDCol0;
-                    tc_mma(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
+                    if (lane == 0) {
+                        // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit
+                        // field: B lies below 256 KB of shared memory)
+                        const uint64_t bdesc0 = b_desc(smem_u32(Bs + h * kBBytes));
+                        const uint32_t dt = tmem + kDCol0;
+                        tc_mma(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        if (s < ksteps)
-                            tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4),
-                                   kIdesc, tmem + kSfOneA, tmem + kSfOneB, 1u);
+                        for (int s = 0; s < 8; ++s) {
+                            if (s < ksteps)
+                                tc_mma(dt, at + s * 8, bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4),
+                                       kIdesc, tmem + kSfOneA, tmem + kSfOneB, 1u);
+                        }
+                        tc_commit(&ctl->d_full);
+                        if (ct == ncols - 1) tc_commit(&ctl->b_empty[h]);  // this half of B is free for the next item
                     }
-                    tc_commit(&ctl->d_full);
+                    __syncwarp();
                     if (ct == ncols - 1) {
-                        tc_commit(&ctl->b_empty[h]);  // this half of B is free for the next item
                         if (h) ++bused1;
                         else ++bused0;
                     }
                     ++tiles;
                 }
                 if (!ok) break;
-                tc_commit(&ctl->a_empty[buf]);
+                release_a = (int)buf;
                 ++fills;
             }
             if (!ok) {
