@@ -700,19 +700,6 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 const int ct = first ? v : v % ncols;
                 const int k0 = k0i + h * kCodedPerHalf + oct * 8;
                 const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
-                // a later source chunk adds its share to the bytes this thread wrote for the earlier
-                // chunks (same lane, same packets): they are read here, before the wait for this
-                // pass's MMAs, all eight loads at once (a load after a store through the same pointer
-                // type would otherwise wait for the previous byte's round trip), packed in two words
-                uint32_t prev0 = 0u, prev1 = 0u;
-                if (!first && (unsigned long long)(c0 + ct) * kColTile + pos < len && nk > 0) {
-                    const uint8_t *q = g.out + (size_t)k0 * len + (size_t)(c0 + ct) * kColTile + pos;
-                    uint32_t b[8];
-#pragma unroll
-                    for (int kp = 0; kp < 8; ++kp) b[kp] = kp < nk ? (uint32_t)q[(size_t)kp * len] : 0u;
-                    prev0 = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-                    prev1 = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-                }
                 if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;
@@ -735,10 +722,25 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 }
                 if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nk > 0) {
                     uint8_t *o = g.out + (size_t)k0 * len + (size_t)(c0 + ct) * kColTile + pos;
+                    if (first) {
 #pragma unroll
-                    for (int kp = 0; kp < 8; ++kp) {
-                        if (kp < nk) *o = (uint8_t)(((kp < 4 ? prev0 : prev1) >> (8 * (kp & 3))) ^ outb[kp]);
-                        o += len;
+                        for (int kp = 0; kp < 8; ++kp) {
+                            if (kp < nk) *o = (uint8_t)outb[kp];
+                            o += len;
+                        }
+                    } else {
+                        // a later source chunk adds its share to the bytes this thread wrote for the
+                        // earlier chunks (same lane, same packets); all eight loads are issued before
+                        // any store (a load after a store through the same pointer type would
+                        // otherwise wait for the previous byte's round trip)
+                        uint32_t prev[8];
+#pragma unroll
+                        for (int kp = 0; kp < 8; ++kp) prev[kp] = kp < nk ? (uint32_t)o[(size_t)kp * len] : 0u;
+#pragma unroll
+                        for (int kp = 0; kp < 8; ++kp) {
+                            if (kp < nk) *o = (uint8_t)(prev[kp] ^ outb[kp]);
+                            o += len;
+                        }
                     }
                 }
                 ++tiles;
