@@ -16,6 +16,7 @@ The C source is compiled on first use (``gcc -O2``) into ``oracle/_build/``.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -46,35 +47,70 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def compile_source(source: str, path: str) -> str:
+    """Compile C source text with the oracle's flags into a shared library at
+    ``path`` (the planted-mistake tests compile altered copies of
+    ``gf_oracle.c`` this way)."""
+    src = path + ".c"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", path, src])
+    return path
+
+
+def source() -> str:
+    """Text of ``gf_oracle.c``."""
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        sz = ctypes.c_size_t
-        lib.gfo_field_ok.argtypes = [ctypes.c_int]
-        lib.gfo_poly.argtypes = [ctypes.c_int]
-        lib.gfo_poly.restype = ctypes.c_uint
-        lib.gfo_mul.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
-        lib.gfo_mul.restype = ctypes.c_uint
-        lib.gfo_inv.argtypes = [ctypes.c_int, ctypes.c_uint]
-        lib.gfo_inv.restype = ctypes.c_uint
-        lib.gfo_mul_table.argtypes = [ctypes.c_int, u8p]
-        for name in ("gfo_region_madd", "gfo_region_mul", "gfo_madd_shuffle", "gfo_madd_imul"):
-            getattr(lib, name).argtypes = [ctypes.c_int, u8p, u8p, ctypes.c_uint, sz]
-        lib.gfo_encode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p]
-        lib.gfo_decode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p,
-                                   u8p, ctypes.POINTER(ctypes.c_int)]
-        lib.gfo_decode.restype = ctypes.c_int
-        lib.gfo_recode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p, u8p,
-                                   u8p]
-        lib.gfo_recode.restype = None
-        lib.gfo_rank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
-        lib.gfo_rank.restype = ctypes.c_int
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _configure(ctypes.CDLL(build()))
+        return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Run every function of this module on another compiled copy of the
+    oracle (a library built by ``compile_source``) inside the ``with`` block."""
+    global _lib
+    other = _configure(ctypes.CDLL(path))
+    with _lock:
+        saved, _lib = _lib, other
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
+
+
+def _configure(lib):
+    """Declare the argument and result types of the oracle's C functions."""
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    sz = ctypes.c_size_t
+    lib.gfo_field_ok.argtypes = [ctypes.c_int]
+    lib.gfo_poly.argtypes = [ctypes.c_int]
+    lib.gfo_poly.restype = ctypes.c_uint
+    lib.gfo_mul.argtypes = [ctypes.c_int, ctypes.c_uint, ctypes.c_uint]
+    lib.gfo_mul.restype = ctypes.c_uint
+    lib.gfo_inv.argtypes = [ctypes.c_int, ctypes.c_uint]
+    lib.gfo_inv.restype = ctypes.c_uint
+    lib.gfo_mul_table.argtypes = [ctypes.c_int, u8p]
+    for name in ("gfo_region_madd", "gfo_region_mul", "gfo_madd_shuffle", "gfo_madd_imul"):
+        getattr(lib, name).argtypes = [ctypes.c_int, u8p, u8p, ctypes.c_uint, sz]
+    lib.gfo_encode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p]
+    lib.gfo_decode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p,
+                               u8p, ctypes.POINTER(ctypes.c_int)]
+    lib.gfo_decode.restype = ctypes.c_int
+    lib.gfo_recode.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, sz, u8p, u8p, u8p, u8p,
+                               u8p]
+    lib.gfo_recode.restype = None
+    lib.gfo_rank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u8p]
+    lib.gfo_rank.restype = ctypes.c_int
+    return lib
 
 
 def _u8(a: np.ndarray):

@@ -107,6 +107,26 @@ def test_rank_deficient_by_hand():
     assert out[:, 0].tolist() == [1, 9]
 
 
+@pytest.mark.parametrize("n", FIELDS)
+def test_used_counts_rows_until_rank_n(n):
+    """The decoder stops once the rank reaches N: `used` is the position of
+    the row that completed the rank, whatever follows it (rows by hand)."""
+    # two unit rows complete the rank of a 2-source generation; the third row is never consumed
+    coef = np.array([[1, 0], [0, 1], [1, 1]], dtype=np.uint8)
+    payload = np.array([[5], [6], [0]], dtype=np.uint8)  # the last row is inconsistent on purpose
+    out, solved, rank, used = oracle.decode(n, coef, payload)
+    assert (rank, used) == (2, 2) and solved.all()
+    assert out[:, 0].tolist() == [5, 6]  # unit rows: the payload bytes themselves, in every field
+    # a repeated row in between is consumed but not innovative
+    coef = np.array([[1, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1], [0, 1, 1]], dtype=np.uint8)
+    out, solved, rank, used = oracle.decode(n, coef, np.zeros((6, 0), dtype=np.uint8))
+    assert (rank, used) == (3, 4)
+    # a stream that never reaches rank N consumes every row
+    coef = np.array([[1, 1, 0], [1, 1, 0], [0, 0, 1]], dtype=np.uint8)
+    out, solved, rank, used = oracle.decode(n, coef, np.zeros((3, 0), dtype=np.uint8))
+    assert (rank, used) == (2, 3) and solved.tolist() == [False, False, True]
+
+
 def _brute_rank(n, M):
     """log_q of the number of distinct vectors in the row space."""
     q = 1 << n
