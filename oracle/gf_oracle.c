@@ -30,7 +30,11 @@
  * exhaustively, multiplication by x as shift-and-reduce, the GF(4) field
  * derived by brute force from the axioms, the paper's two madd algorithms
  * restated independently, encode/decode round trips, brute-force rank on
- * tiny matrices and the full-rank probability of random matrices).
+ * tiny matrices and the full-rank probability of random matrices).  The
+ * planted-mistake tests compile altered copies of this file (a wrong
+ * polynomial, a dropped reduction step, a misplaced word, a transposed
+ * matrix, a missing elimination step, ...) and check that each one fails
+ * at least one of those pins.
  */
 #include <stddef.h>
 #include <stdint.h>
