@@ -1,0 +1,102 @@
+"""The bit-sliced formulation of Eq. 2, checked on the CPU against the oracle.
+
+The tensor-core encode rests on the identity of section IV-B,
+c * a = XOR_j a_j * (c * x^j): multiplication by c is a GF(2)-linear map, an
+8 x 8 bit matrix on a byte (block-diagonal with n x n blocks for GF(2^n),
+n < 8, since a byte holds 8/n words multiplied by the same c).  Eq. 2 then
+becomes one binary matrix product whose integer sums are reduced mod 2, and
+the kernel computes those sums in FP32 above a bias of 2^23, reading the
+parity from the low mantissa bits.  These tests restate that arithmetic with
+numpy (no CUDA) and compare it with the oracle's encode, so the formulation
+itself is pinned independently of the kernel."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_02871_gb300 import synth
+
+FIELDS = (1, 2, 4, 8)
+
+
+def bit_matrix(n, c):
+    """8 x 8 matrix over GF(2): entry [r][j] = bit r of the product byte when
+    the input byte is the unit byte with bit j set (words of n bits)."""
+    M = np.zeros((8, 8), dtype=np.int64)
+    for j in range(8):
+        word, bit = divmod(j, n)
+        prod = oracle.mul(n, c, 1 << bit) << (word * n)  # c * x^bit, in the same word
+        for r in range(8):
+            M[r, j] = (prod >> r) & 1
+    return M
+
+
+def bits(a):
+    """Bit planes of a byte array: shape (..., 8), plane j = bit j."""
+    return (a[..., None] >> np.arange(8)) & 1
+
+
+@pytest.mark.parametrize("n", FIELDS)
+def test_bit_matrix_is_the_product(n):
+    q = 1 << n
+    for c in range(q):
+        M = bit_matrix(n, c)
+        for a in range(256):
+            prod = oracle.region_mul(n, np.array([a], dtype=np.uint8), c)[0]
+            assert np.array_equal((M @ bits(np.array(a))) % 2, bits(np.array(prod)))
+
+
+@pytest.mark.parametrize("n", (1, 2, 4))
+def test_small_fields_are_block_diagonal(n):
+    for c in range(1 << n):
+        M = bit_matrix(n, c)
+        for r in range(8):
+            for j in range(8):
+                if r // n != j // n:
+                    assert M[r, j] == 0
+
+
+@pytest.mark.parametrize("n", FIELDS)
+def test_encode_as_one_binary_matrix_product(n):
+    g = synth.choice(31, n)
+    N, K, L = 70, 37, 53  # more than one 64-source chunk, ragged everywhere
+    src = synth.random_bytes(g, (N, L))
+    coef = synth.coefficients(g, n, (K, N), nonzero=False)
+    # A: (8N x L) source bit planes; B: (8K x 8N) block matrix of the coefficients' bit matrices
+    A = bits(src).transpose(0, 2, 1).reshape(8 * N, L)
+    B = np.zeros((8 * K, 8 * N), dtype=np.int64)
+    mats = {c: bit_matrix(n, c) for c in range(1 << n)}
+    for k in range(K):
+        for i in range(N):
+            B[8 * k:8 * k + 8, 8 * i:8 * i + 8] = mats[int(coef[k, i])]
+    S = B @ A  # integer sums, at most 8N terms each
+    assert S.max() <= 8 * N
+    # the sums of the 64-source chunks, reduced separately and XORed, give the same parities
+    chunks = [B[:, 8 * i0:8 * min(N, i0 + 64)] @ A[8 * i0:8 * min(N, i0 + 64)] for i0 in range(0, N, 64)]
+    par = np.zeros_like(S)
+    for part in chunks:
+        par ^= part & 1
+    assert np.array_equal(par, S & 1)
+    out_bits = (S & 1).reshape(K, 8, L)
+    out = (out_bits << np.arange(8)[None, :, None]).sum(axis=1).astype(np.uint8)
+    assert np.array_equal(out, oracle.encode(n, src, coef))
+
+
+def test_fp32_sums_above_the_bias_are_exact():
+    """A 64-source chunk sums at most 512 products of 0/1 values; added to 2^23
+    in FP32 in any order the result stays an integer below 2^24, so the low
+    16 bits of its encoding are the sum and bit 0 is the parity."""
+    g = synth.choice(32, 0)
+    for _ in range(200):
+        terms = g.integers(0, 2, size=512).astype(np.float32)
+        order = g.permutation(512)
+        acc = np.float32(2.0 ** 23)
+        for t in terms[order]:
+            acc = np.float32(acc + t)
+        exact = int(terms.sum())
+        low16 = int(np.array(acc, dtype=np.float32).view(np.uint32)) & 0xFFFF
+        assert low16 == exact and (low16 & 1) == (exact & 1)
+    # the largest chunk sum: every product 1
+    acc = np.float32(2.0 ** 23)
+    for _ in range(512):
+        acc = np.float32(acc + np.float32(1.0))
+    assert int(np.array(acc, dtype=np.float32).view(np.uint32)) & 0xFFFF == 512
