@@ -8,18 +8,23 @@
 //   1. coefficient phase (one CTA per generation, decode_coef_kernel):
 //      progressive Gauss-Jordan over the coding vectors, rows in arrival
 //      order, each row augmented with its own unit vector to record the
-//      transform.  Per received row: eliminate the current pivots (the
-//      stored rows are reduced, so this is one parallel vector-matrix
-//      product), find the pivot (first nonzero coefficient, warp ballot),
-//      drop the row if there is none, normalise it by the pivot's inverse,
-//      eliminate its pivot column from every stored row, store it.  It stops
-//      at rank N.  Row operations are split-table region madds on 32-bit
-//      words in shared memory (gf::ByteMap); in the elimination of the new
-//      row each warp sums the products of a share of the stored rows in
-//      registers and the warps' sums are combined with shared-memory
-//      atomicXor.  Output: X (N x R), where row p of X expresses decoded
-//      source p in the received rows (zero if p is not determined), plus
-//      rank, rows consumed and per-source flags.
+//      transform; a row's pivot is its first nonzero coefficient once the
+//      earlier pivots are eliminated, a row without one is dropped, and it
+//      stops at rank N.  Rows are taken in batches of kDecBatch: the stored
+//      rows are reduced, so eliminating them from every batch row is one
+//      parallel product in which each stored word's prmt selectors serve
+//      all the batch rows (each warp sums a share of the stored rows in
+//      registers, shared-memory atomicXor combines the warps); then the
+//      batch is settled row by row in arrival order (pivot by warp ballot,
+//      normalisation by the pivot's inverse, the pivot column eliminated
+//      from every other batch row at once), and one sweep back-substitutes
+//      the batch's new pivots into the stored rows.  The stored rows end in
+//      the same reduced form as row-by-row elimination gives (that form is
+//      unique), so the outputs do not depend on the batching.  Row
+//      operations are split-table region madds on 32-bit words in shared
+//      memory (gf::ByteMap).  Output: X (N x R), where row p of X expresses
+//      decoded source p in the received rows (zero if p is not determined),
+//      plus rank, rows consumed and per-source flags.
 //   2. payload phase: out = X * payload, i.e. an encode (Eq. 2) of N packets
 //      from the R received packets, run by the batched encode.
 //
@@ -36,6 +41,7 @@
 namespace gf {
 
 constexpr int kDecThreads = 1024;
+constexpr int kDecBatch = 4;  // arriving rows eliminated against the stored rows together
 
 struct alignas(16) DecMap {
     ByteMap m;
@@ -50,44 +56,60 @@ size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem)
     b += align_up((size_t)(1u << field) * sizeof(DecMap), 16);  // tables
     b += 256;                                                  // inverses
     b += align_up((size_t)N * sizeof(int), 16) * 2;            // pivrow, pcol
-    b += align_up((size_t)N, 16) * 2;                          // fsnap, gsnap
-    b += (size_t)W;                                            // cur
+    b += align_up((size_t)N * kDecBatch, 16) * 2;              // F, G snapshots
+    b += (size_t)W * kDecBatch;                                // the batch's rows
     if (rows_in_smem) b += (size_t)N * W;
     return b;
 }
 
-// cur[j0 + 4 lane .. +3] ^= sum over stored rows t = warp (mod the warp count)
-// of f_t * rows[t][same words]: one 16-byte shared load per row and lane, the
-// row's byte map loaded once for four words; then one atomicXor per word and
-// warp combines the warps (nw, j0 multiples of 4)
-__device__ __forceinline__ void eliminate_rows(uint32_t *cur, const uint32_t *rows, const uint8_t *fsnap,
-                                               const DecMap *tab, int rank, int nw, int nw_r, int j0, int warp,
-                                               int lane)
+// cur[b][j0 + 2 lane .. +1] ^= sum over stored rows t = warp (mod the warp
+// count) of F[b][t] * rows[t][same words], for the nb rows b of the batch:
+// the prmt selectors of a stored word are computed once and applied with
+// each row's coefficient (the point of eliminating rows in batches); then one
+// atomicXor per word, row and warp combines the warps (nw_r, j0 even)
+__device__ __forceinline__ void eliminate_batch(uint32_t *cur, const uint32_t *rows, const uint8_t *F, int N,
+                                                const DecMap *tab, int rank, int nw, int nw_r, int nb, int j0,
+                                                int warp, int lane)
 {
-    const int j = j0 + 4 * lane;
+    const int j = j0 + 2 * lane;
     if (j >= nw_r) return;  // lanes past the live words have nothing to add (no warp-wide operations below)
-    uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
+    uint32_t acc[kDecBatch][2];
+#pragma unroll
+    for (int b = 0; b < kDecBatch; ++b) acc[b][0] = acc[b][1] = 0u;
     for (int t = warp; t < rank; t += kDecThreads / 32) {
-        const uint32_t f = fsnap[t];
-        if (!f) continue;
-        const ByteMap m = tab[f].m;
-        const uint4 w = *reinterpret_cast<const uint4 *>(rows + (size_t)t * nw + j);
-        a0 ^= apply_word(m, w.x);
-        a1 ^= apply_word(m, w.y);
-        a2 ^= apply_word(m, w.z);
-        a3 ^= apply_word(m, w.w);
+        uint32_t f[kDecBatch];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int b = 0; b < kDecBatch; ++b) {
+            f[b] = b < nb ? (uint32_t)F[b * N + t] : 0u;
+            any |= f[b];
+        }
+        if (!any) continue;
+        const uint2 w = *reinterpret_cast<const uint2 *>(rows + (size_t)t * nw + j);
+        const Sel s0 = make_sel(w.x), s1 = make_sel(w.y);
+#pragma unroll
+        for (int b = 0; b < kDecBatch; ++b) {
+            if (!f[b]) continue;
+            const ByteMap m = tab[f[b]].m;
+            acc[b][0] ^= apply(m, s0);
+            acc[b][1] ^= apply(m, s1);
+        }
     }
-    if (a0) atomicXor(&cur[j], a0);
-    if (a1) atomicXor(&cur[j + 1], a1);
-    if (a2) atomicXor(&cur[j + 2], a2);
-    if (a3) atomicXor(&cur[j + 3], a3);
+#pragma unroll
+    for (int b = 0; b < kDecBatch; ++b) {
+        if (b >= nb) break;
+        if (acc[b][0]) atomicXor(&cur[b * nw + j], acc[b][0]);
+        if (acc[b][1]) atomicXor(&cur[b * nw + j + 1], acc[b][1]);
+    }
 }
 
 __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *__restrict__ gens)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_rank, s_pivot, s_used;
+    __shared__ int s_rank, s_pivot, s_used, s_knew;
     __shared__ uint32_t s_inv;
+    __shared__ int s_newb[kDecBatch], s_newc[kDecBatch];  // the batch's pivot rows and their columns
+    __shared__ uint8_t s_g[kDecBatch];                    // each batch row's value in the new pivot column
 
     const DecGen g = gens[blockIdx.x];
     const int N = g.N, R = g.R, W = g.W, n = g.field;
@@ -105,14 +127,15 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     p += align_up((size_t)N * sizeof(int), 16);
     int *pcol = reinterpret_cast<int *>(p);    // stored row -> pivot column
     p += align_up((size_t)N * sizeof(int), 16);
-    uint8_t *fsnap = p;
-    p += align_up((size_t)N, 16);
-    uint8_t *gsnap = p;
-    p += align_up((size_t)N, 16);
-    uint32_t *cur = reinterpret_cast<uint32_t *>(p);
-    p += W;
+    uint8_t *F = p;                            // F[b * N + t]: batch row b in stored row t's pivot column
+    p += align_up((size_t)N * kDecBatch, 16);
+    uint8_t *G = p;                            // G[t * kDecBatch + k]: stored row t in the k-th new pivot column
+    p += align_up((size_t)N * kDecBatch, 16);
+    uint32_t *cur = reinterpret_cast<uint32_t *>(p);  // batch row b at cur + b * nw
+    p += (size_t)W * kDecBatch;
     uint32_t *rows = g.grows ? reinterpret_cast<uint32_t *>(g.grows) : reinterpret_cast<uint32_t *>(p);
     const uint8_t *curb = reinterpret_cast<const uint8_t *>(cur);
+    const uint8_t *rowsb = reinterpret_cast<const uint8_t *>(rows);
 
     for (uint32_t c = tid; c < q; c += blockDim.x) {
         tab[c].m = make_bytemap(n, c);
@@ -125,121 +148,147 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     }
     __syncthreads();
 
-    // coefficient bytes of the next arriving row, prefetched a row ahead: the
-    // four loads are issued here and only combined into a word when the row
-    // is used, a whole row step later, so their latency is hidden (a thread
-    // owns coefficient word tid; N <= 4 * kDecThreads)
-    uint32_t nb[4];
-    auto fetch = [&](int rr) {
+    for (int r0 = 0;; r0 += kDecBatch) {
+        const int rank = s_rank;  // stored rows before this batch
+        if (r0 >= R || rank >= N) break;
+        const int nb = min(kDecBatch, R - r0);
+        // Rows received so far carry transform entries only in columns N .. N+r0+nb-1 (each row
+        // starts as its own unit vector), so every word past that is zero in the stored rows and
+        // in the batch: the row operations stop at word nw_r.
+        const int nw_r = min(nw, (N + r0 + nb + 15) / 16 * 4);  // whole 16-byte groups
+        // 1. the batch's rows: [coef | unit vector e_r] over the live words
+        for (int idx = tid; idx < nb * nw_r; idx += blockDim.x) {
+            const int b = idx / nw_r, j = idx - b * nw_r;
+            uint32_t v = 0u;
 #pragma unroll
-        for (int b = 0; b < 4; ++b)
-            nb[b] = (rr < R && 4 * tid + b < N) ? (uint32_t)__ldg(g.coef + (size_t)rr * N + 4 * tid + b) : 0u;
-    };
-    fetch(0);
-    int r = 0;
-    for (; r < R; ++r) {
-        const int rank = s_rank;
-        if (rank >= N) break;
-        // 1. the arriving row: [coef | unit vector e_r]
-        const uint32_t mine = nb[0] | (nb[1] << 8) | (nb[2] << 16) | (nb[3] << 24);
-        fetch(r + 1);
-        for (int j = tid; j < nw; j += blockDim.x) {
-            uint32_t v = j == tid ? mine : 0u;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (4 * j + b == N + r) v |= 1u << (8 * b);
-            cur[j] = v;
+            for (int x = 0; x < 4; ++x) {
+                const int col = 4 * j + x;
+                const uint32_t byte = col < N ? (uint32_t)__ldg(g.coef + (size_t)(r0 + b) * N + col)
+                                              : (col == N + r0 + b ? 1u : 0u);
+                v |= byte << (8 * x);
+            }
+            cur[b * nw + j] = v;
+        }
+        if (tid == 0) s_knew = 0;
+        __syncthreads();
+        // 2. each batch row's value in the pivot column of each stored row
+        for (int idx = tid; idx < nb * rank; idx += blockDim.x) {
+            const int b = idx / rank, t = idx - b * rank;
+            F[b * N + t] = curb[b * W + pcol[t]];
         }
         __syncthreads();
-        // 2. the arriving row's value in the pivot column of each stored row
-        for (int t = tid; t < rank; t += blockDim.x) fsnap[t] = curb[pcol[t]];
-        __syncthreads();
-        // 3. cur -= sum_t f_t * row(t): stored rows are reduced, so every f_t is
-        //    the arriving row's own value in row t's pivot column.  Warp w takes
-        //    the stored rows t = w (mod the warp count); each lane accumulates its word
-        //    columns (up to four, as many as the row is wide, in independent
-        //    registers) and one atomicXor per word and warp combines the warps.
-        // Rows received so far carry transform entries only in columns N .. N+r
-        // (each row starts as its own unit vector), so every word past
-        // column N+r is zero in the stored rows and in the arriving row:
-        // the row operations stop at word nw_r.
-        const int nw_r = min(nw, (N + r + 1 + 15) / 16 * 4);  // whole 16-byte groups
+        // 3. cur[b] -= sum_t F[b][t] * row(t) for every batch row: the stored rows are reduced,
+        //    so every F[b][t] is row b's own value in row t's pivot column
         if (rank > 0)
-            for (int j0 = 0; j0 < nw_r; j0 += 128) eliminate_rows(cur, rows, fsnap, tab, rank, nw, nw_r, j0, warp, lane);
+            for (int j0 = 0; j0 < nw_r; j0 += 64) eliminate_batch(cur, rows, F, N, tab, rank, nw, nw_r, nb, j0, warp, lane);
         __syncthreads();
-        // 4. pivot: first nonzero coefficient (warp 0, ballot over words)
-        if (warp == 0) {
-            int piv = -1;
-            const int ncw = (N + 3) / 4;
-            for (int base = 0; base < ncw && piv < 0; base += 32) {
-                const int j = base + lane;
-                uint32_t v = 0;
-                if (j < ncw) {
-                    v = cur[j];
-                    const int valid = N - 4 * j;  // bytes of this word inside [0, N)
-                    if (valid < 4) v &= (1u << (8 * valid)) - 1u;
+        // 4. Gauss-Jordan within the batch, in arrival order: each new pivot row is normalised and
+        //    its pivot column eliminated from every other batch row at once (the earlier pivot
+        //    rows stay reduced, the later rows arrive at their turn already reduced)
+        for (int b = 0; b < nb; ++b) {
+            // 4a. pivot: first nonzero coefficient of row b (warp 0, ballot over words); the
+            //     other batch rows' values in that column are snapshotted with it
+            if (warp == 0) {
+                const uint32_t *row = cur + b * nw;
+                int piv = -1;
+                const int ncw = (N + 3) / 4;
+                for (int base = 0; base < ncw && piv < 0; base += 32) {
+                    const int j = base + lane;
+                    uint32_t v = 0;
+                    if (j < ncw) {
+                        v = row[j];
+                        const int valid = N - 4 * j;  // bytes of this word inside [0, N)
+                        if (valid < 4) v &= (1u << (8 * valid)) - 1u;
+                    }
+                    const uint32_t ball = __ballot_sync(0xffffffffu, v != 0);
+                    if (ball) {
+                        const int src = __ffs(ball) - 1;
+                        const uint32_t vw = __shfl_sync(0xffffffffu, v, src);
+                        piv = 4 * (base + src) + (__ffs(vw) - 1) / 8;
+                    }
                 }
-                const uint32_t ball = __ballot_sync(0xffffffffu, v != 0);
-                if (ball) {
-                    const int src = __ffs(ball) - 1;
-                    const uint32_t vw = __shfl_sync(0xffffffffu, v, src);
-                    piv = 4 * (base + src) + (__ffs(vw) - 1) / 8;
+                if (lane == 0) {
+                    s_pivot = piv;
+                    if (piv >= 0) s_inv = invt[curb[b * W + piv]];
+                    s_used = r0 + b + 1;
+                }
+                if (piv >= 0 && lane < nb) s_g[lane] = lane != b ? curb[lane * W + piv] : 0;
+            }
+            __syncthreads();
+            const int piv = s_pivot;
+            // 4b. normalise row b and eliminate its pivot column from the other batch rows (a
+            //     thread owns a word column of every batch row); a row without a pivot is not
+            //     innovative and is dropped
+            if (piv >= 0) {
+                const ByteMap m = tab[s_inv].m;
+                for (int j = tid; j < nw_r; j += blockDim.x) {
+                    const uint32_t pv = apply_word(m, cur[b * nw + j]);
+                    cur[b * nw + j] = pv;
+                    const Sel sel = make_sel(pv);
+#pragma unroll
+                    for (int o = 0; o < kDecBatch; ++o) {
+                        if (o >= nb) break;
+                        const uint32_t go = s_g[o];
+                        if (o != b && go) cur[o * nw + j] ^= apply(tab[go].m, sel);
+                    }
                 }
             }
-            if (lane == 0) {
-                s_pivot = piv;
-                if (piv >= 0) s_inv = invt[curb[piv]];
+            if (tid == 0 && piv >= 0) {
+                const int knew = s_knew;
+                s_newb[knew] = b;
+                s_newc[knew] = piv;
+                s_knew = knew + 1;
+                s_rank = s_rank + 1;
             }
+            __syncthreads();  // also keeps the pivot shared state of this row until every thread has read it
+            if (s_rank >= N) break;
         }
+        const int knew = s_knew;
+        // 5. back-substitution of the batch's pivots into the stored rows, one sweep: G first
+        if (knew > 0 && rank > 0)
+            for (int idx = tid; idx < rank * knew; idx += blockDim.x) {
+                const int t = idx / knew, k = idx - t * knew;
+                G[t * kDecBatch + k] = rowsb[(size_t)t * W + s_newc[k]];
+            }
         __syncthreads();
-        const int piv = s_pivot;
-        if (piv < 0) continue;  // not innovative
-        // 5. normalise
-        {
-            const ByteMap m = tab[s_inv].m;
-            for (int j = tid; j < nw_r; j += blockDim.x) cur[j] = apply_word(m, cur[j]);
-        }
-        // 6. column `piv` of every stored row
-        for (int s = tid; s < rank; s += blockDim.x)
-            gsnap[s] = reinterpret_cast<const uint8_t *>(rows + (size_t)s * nw)[piv];
-        __syncthreads();
-        // 7. back-substitution into the stored rows, 8. store the new row.
-        //    A thread owns a word column j (its prmt selectors computed once)
-        //    and walks a share of the stored rows.
-        {
+        //    a thread owns a word column j (the prmt selectors of each new pivot row's words
+        //    computed once) and walks a share of the stored rows
+        if (knew > 0 && rank > 0) {
             const int ng = nw_r / 4;                               // 16-byte word groups
             const int per = max(1, kDecThreads / max(ng, 1));      // threads per group
             const int groups = kDecThreads / per;
             const int g_start = tid % groups, part = tid / groups;
             for (int gq = g_start; gq < ng && part < per; gq += groups) {
                 const int j = 4 * gq;
-                const uint4 cw = *reinterpret_cast<const uint4 *>(cur + j);
-                const Sel s0 = make_sel(cw.x), s1 = make_sel(cw.y), s2 = make_sel(cw.z), s3 = make_sel(cw.w);
-                for (int s = part; s < rank; s += per) {
-                    const uint32_t f = gsnap[s];
-                    if (!f) continue;
-                    const ByteMap m = tab[f].m;
-                    uint4 *rw = reinterpret_cast<uint4 *>(rows + (size_t)s * nw + j);
-                    uint4 w = *rw;
-                    w.x ^= apply(m, s0);
-                    w.y ^= apply(m, s1);
-                    w.z ^= apply(m, s2);
-                    w.w ^= apply(m, s3);
-                    *rw = w;
+                for (int k = 0; k < knew; ++k) {
+                    const uint4 cw = *reinterpret_cast<const uint4 *>(cur + s_newb[k] * nw + j);
+                    const Sel s0 = make_sel(cw.x), s1 = make_sel(cw.y), s2 = make_sel(cw.z), s3 = make_sel(cw.w);
+                    for (int s = part; s < rank; s += per) {
+                        const uint32_t f = G[s * kDecBatch + k];
+                        if (!f) continue;
+                        const ByteMap m = tab[f].m;
+                        uint4 *rw = reinterpret_cast<uint4 *>(rows + (size_t)s * nw + j);
+                        uint4 w = *rw;
+                        w.x ^= apply(m, s0);
+                        w.y ^= apply(m, s1);
+                        w.z ^= apply(m, s2);
+                        w.w ^= apply(m, s3);
+                        *rw = w;
+                    }
                 }
-                if (part == 0) *reinterpret_cast<uint4 *>(rows + (size_t)rank * nw + j) = cw;
             }
-            for (int j = nw_r + tid; j < nw; j += blockDim.x) rows[(size_t)rank * nw + j] = 0u;
         }
-        __syncthreads();
-        if (tid == 0) {
-            pivrow[piv] = rank;
-            pcol[rank] = piv;
-            s_rank = rank + 1;
+        // 6. store the batch's pivot rows after the stored ones (zero past the live words)
+        for (int idx = tid; idx < knew * nw; idx += blockDim.x) {
+            const int k = idx / nw, j = idx - k * nw;
+            rows[(size_t)(rank + k) * nw + j] = j < nw_r ? cur[s_newb[k] * nw + j] : 0u;
+        }
+        if (tid < knew) {
+            pivrow[s_newc[tid]] = rank + tid;
+            pcol[rank + tid] = s_newc[tid];
         }
         __syncthreads();
     }
-    if (tid == 0) s_used = r;
     __syncthreads();
 
     // outputs: X row p = transform part of the row with pivot p if that row

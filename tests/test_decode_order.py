@@ -17,7 +17,7 @@ from paper_1909_02871_gb300 import synth
 FIELDS = (1, 2, 4, 8)
 
 
-def batched_decode(n, coef, payload, B):
+def batched_decode(n, coef, payload, B, right_looking=False):
     # T[f][v]: f times every word of byte v (payload bytes hold 8/n words; a
     # coefficient is word 0 of its byte), from the oracle's region multiply
     T = np.stack([oracle.region_mul(n, np.arange(256, dtype=np.uint8), f) for f in range(1 << n)]).astype(np.int64)
@@ -45,20 +45,27 @@ def batched_decode(n, coef, payload, B):
         new = []                              # (batch row, pivot column)
         stop = False
         for b in range(nb):
-            f = [cur[b, c] for _, c in new]
-            for (b2, _), fb in zip(new, f):
-                if fb:
-                    cur[b] = madd(cur[b], fb, cur[b2])
+            if not right_looking:             # settle row b against the batch's pivots so far
+                f = [cur[b, c] for _, c in new]
+                for (b2, _), fb in zip(new, f):
+                    if fb:
+                        cur[b] = madd(cur[b], fb, cur[b2])
             used = r0 + b + 1
             nz = np.nonzero(cur[b, :N])[0]
             if nz.size == 0:
                 continue
             piv = int(nz[0])
             cur[b] = T[inv[cur[b, piv]]][cur[b]]
-            for b2, _ in new:                 # keep the batch's pivot rows reduced
-                g = cur[b2, piv]
-                if g:
-                    cur[b2] = madd(cur[b2], g, cur[b])
+            if right_looking:                 # the new pivot column leaves every other batch row
+                gs = cur[:, piv].copy()
+                for o in range(nb):
+                    if o != b and gs[o]:
+                        cur[o] = madd(cur[o], gs[o], cur[b])
+            else:
+                for b2, _ in new:             # keep the batch's pivot rows reduced
+                    g = cur[b2, piv]
+                    if g:
+                        cur[b2] = madd(cur[b2], g, cur[b])
             new.append((b, piv))
             rank += 1
             if rank == N:
@@ -102,12 +109,16 @@ def _streams(n, g):
 
 
 @pytest.mark.parametrize("n", FIELDS)
-@pytest.mark.parametrize("B", [1, 2, 3, 8])
-def test_batched_order_gives_the_oracles_outputs(n, B):
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("right_looking", [False, True])
+def test_batched_order_gives_the_oracles_outputs(n, B, right_looking):
+    """right_looking: each new pivot row's column is eliminated from every other
+    row of the batch at once (the order the CUDA decoder uses); otherwise each
+    row is settled against the batch's earlier pivots when its turn comes."""
     g = synth.choice(61, n, B)
     for coef, payload in _streams(n, g):
         ref_out, ref_solved, ref_rank, ref_used = oracle.decode(n, coef, payload)
-        out, solved, rank, used = batched_decode(n, coef, payload, B)
+        out, solved, rank, used = batched_decode(n, coef, payload, B, right_looking)
         assert (rank, used) == (ref_rank, ref_used)
         assert np.array_equal(solved, ref_solved)
         assert np.array_equal(out, ref_out)
