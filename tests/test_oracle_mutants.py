@@ -79,6 +79,17 @@ MISTAKES = [
     ("decode does not stop at rank N", "for (r = 0; r < R && rank < N; r++)", "for (r = 0; r < R; r++)"),
     ("decode reports every pivot row as solved", "{ unit = 0; break; }", "{ break; }"),
     ("recode composes the vectors transposed", "coef_in[(size_t)r * N + i]", "coef_in[(size_t)i * R + r]"),
+    # off by one at a loop boundary
+    ("madd skips the last byte", "    for (k = 0; k < len; k++) {\n        unsigned byte = src[k], acc = dst[k];",
+     "    for (k = 0; k + 1 < len; k++) {\n        unsigned byte = src[k], acc = dst[k];"),
+    ("madd skips the last word of a byte",
+     "for (j = 0; j < words; j++) {\n            unsigned w = (byte >> (j * n)) & mask;\n            acc ^=",
+     "for (j = 0; j + 1 < words; j++) {\n            unsigned w = (byte >> (j * n)) & mask;\n            acc ^="),
+    ("imul restatement drops the last tail byte", "    for (; k < len; k++) {", "    for (; k + 1 < len; k++) {"),
+    ("encode skips the last source", "        for (i = 0; i < N; i++)\n            gfo_region_madd(n, acc, src",
+     "        for (i = 0; i + 1 < N; i++)\n            gfo_region_madd(n, acc, src"),
+    ("recode skips the last held packet", "            for (r = 0; r < R; r++)\n                acc ^= gfo_mul(n, mix",
+     "            for (r = 0; r + 1 < R; r++)\n                acc ^= gfo_mul(n, mix"),
 ]
 
 
