@@ -1,13 +1,15 @@
 """GPU parity of the batched encode (Eq. 2) against the oracle (bit-exact),
 through the C ABI: single generation, ragged/uneven batches, every table
 tile shape, the bit-sliced tensor-core path, plans and CUDA graph replay,
-and the full 4096 x 64 x 1500 B batch on sampled generations."""
+the full 4096 x 64 x 1500 B batch (every generation) and packets of up to
+64 KiB."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1909_02871_gb300 import gf, synth
 
+import oracle_pool
 from gpu_util import dev, to_dev, to_host, torch
 
 pytestmark = pytest.mark.gpu
@@ -170,10 +172,11 @@ def test_plan_and_graph_replay():
     plan.close()
 
 
-def test_full_uniform_batch_sampled():
+def test_full_uniform_batch_every_generation():
     """The 4096 x (N=64 x 1500 B) GF(256) batch, K = 64, in the launch the
-    benchmark times (path chosen by the autotuner); sampled generations are
-    compared with the oracle."""
+    benchmark times (path chosen by the autotuner): every generation compared
+    with the oracle (run on every host core); the table path's launch is
+    compared with it byte for byte."""
     b = synth.uniform_batch()
     G, N, L = b.src.shape
     K = b.coef.shape[1]
@@ -181,12 +184,34 @@ def test_full_uniform_batch_sampled():
     coef = to_dev(b.coef)
     out = torch.empty((G, K, L), dtype=torch.uint8, device=dev())
     gens = [(8, N, K, L, src[i], coef[i], out[i]) for i in range(G)]
-    for path in (gf.PATH_AUTO, gf.PATH_TABLE):
-        out.fill_(0)
-        gf.gf_encode_batched(gens, path=path)
-        torch.cuda.synchronize()
-        for i in (0, 1, 2047, 4095):
-            assert np.array_equal(out[i].cpu().numpy(), oracle.encode(8, b.src[i], b.coef[i])), (path, i)
+    out.fill_(0)
+    gf.gf_encode_batched(gens, path=gf.PATH_AUTO)
+    got = to_host(out)
+    bad = oracle_pool.mismatches(lambda i: np.array_equal(got[i], oracle.encode(8, b.src[i], b.coef[i])), range(G))
+    assert not bad, f"{len(bad)} generations differ from the oracle, first {bad[:8]}"
+    out.fill_(0)
+    gf.gf_encode_batched(gens, path=gf.PATH_TABLE)
+    torch.cuda.synchronize()
+    assert torch.equal(out, torch.from_numpy(got).to(dev())), "table path differs from the benchmarked launch"
+
+
+@pytest.mark.parametrize("path", [gf.PATH_TABLE, gf.PATH_BITSLICED])
+@pytest.mark.parametrize("field", FIELDS)
+def test_fig1_packet_sizes(field, path):
+    """The packet sizes of the paper's Fig. 1 sweep beyond 4 KiB: generations
+    of N = 16 sources and K = 16 coded packets of 8, 16, 32 and 64 KiB (and
+    a ragged 64 KiB - 3), several generations per launch, on both paths."""
+    if path == gf.PATH_BITSLICED and not _bitsliced_ok():
+        pytest.skip("bit-sliced path unavailable")
+    g = synth.choice(63, field, path)
+    items = []
+    for L in (8 << 10, 16 << 10, 32 << 10, 64 << 10, (64 << 10) - 3):
+        for _ in range(2):
+            items.append((field, synth.random_bytes(g, (16, L)), synth.coefficients(g, field, (16, 16), nonzero=True)))
+    outs = _run(items, path=path)
+    bad = oracle_pool.mismatches(lambda j: np.array_equal(outs[j], oracle.encode(field, items[j][1], items[j][2])),
+                                 range(len(items)))
+    assert not bad, [items[j][1].shape for j in bad]
 
 
 def test_host_encoder_pipelined_steps():
