@@ -32,6 +32,7 @@
 // operations gives exactly the result of eliminating on the payloads row by
 // row.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "gf_decode.h"
@@ -318,17 +319,44 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
 // host side
 // ---------------------------------------------------------------------------
 
-static size_t smem_limit()
+// Largest dynamic shared memory a decode CTA may use on the current device
+// (the opt-in limit less room for the kernel's static shared memory).
+size_t decode_smem_limit()
 {
-    static int cached = 0;
-    if (!cached) {
+    static std::mutex mu;
+    static int cached[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return 48 * 1024 - 1024;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[dev]) {
         int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device()) != cudaSuccess ||
-            v <= 0)
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
             v = 48 * 1024;
-        cached = v;
+        cached[dev] = v;
     }
-    return (size_t)cached - 1024;  // room for the kernel's static shared memory
+    return (size_t)cached[dev] - 1024;
+}
+
+// decode_coef_kernel's dynamic shared-memory limit, raised once per device to
+// decode_smem_limit() (the attribute belongs to the function, not to a launch, so
+// it is never lowered for a smaller launch).
+static int configure_decode_coef()
+{
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return GF_ENOTSUP;
+    const size_t limit = decode_smem_limit();
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(decode_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return GF_ECUDA;
+        }
+        done[dev] = true;
+    }
+    return GF_OK;
 }
 
 int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
@@ -338,7 +366,7 @@ int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
     w.gens.resize(n_gens);
     std::vector<EncGen> apply(n_gens);
     size_t x_bytes = 0, grow_bytes = 0;
-    const size_t limit = smem_limit();
+    const size_t limit = decode_smem_limit();
     for (int i = 0; i < n_gens; ++i) {
         const gf_dec_t &d = gens[i];
         if (!field_ok(d.field) || d.n_src < 0 || d.n_src > kMaxDecodeN || d.n_recv < 0 ||
@@ -399,24 +427,19 @@ int place_decode(DecodeWork &w, char *dev_x, char *dev_rows)
 int launch_decode_coef(const DecodeWork &w, const DecGen *d_gens, cudaStream_t stream)
 {
     if (w.gens.empty()) return GF_OK;
-    if (w.smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(decode_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem) !=
-            cudaSuccess)
-            return GF_ECUDA;
-    }
+    const int st = configure_decode_coef();
+    if (st != GF_OK) return st;
     decode_coef_kernel<<<(unsigned)w.gens.size(), kDecThreads, w.smem, stream>>>(d_gens);
     return cuda_status(cudaGetLastError());
 }
 
-// Launch the coefficient phase on descriptors already in device memory.
+// Launch the coefficient phase on descriptors already in device memory
+// (smem <= decode_smem_limit()).
 int launch_decode_coef_raw(const DecGen *d_gens, int n_gens, size_t smem, cudaStream_t stream)
 {
     if (n_gens == 0) return GF_OK;
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(decode_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return GF_ECUDA;
-    }
+    const int st = configure_decode_coef();
+    if (st != GF_OK) return st;
     decode_coef_kernel<<<(unsigned)n_gens, kDecThreads, smem, stream>>>(d_gens);
     return cuda_status(cudaGetLastError());
 }

@@ -43,5 +43,6 @@ size_t decode_stage_bytes(const DecodeWork &w);
 size_t stage_decode(DecodeWork &w, char *host, char *dev_base, size_t off, WorkCounter *counters);
 int launch_decode(const DecodeWork &w, cudaStream_t stream);
 size_t dec_smem_bytes(int field, int N, int W, bool rows_in_smem);
+size_t decode_smem_limit();  // largest dynamic shared memory of a decode CTA on this device
 
 }  // namespace gf

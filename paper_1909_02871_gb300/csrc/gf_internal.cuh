@@ -162,6 +162,8 @@ __device__ __forceinline__ void fill_tables(ByteMap *tab)
 // ------------------------------------------------------------------------
 inline bool field_ok(int n) { return n == 1 || n == 2 || n == 4 || n == 8; }
 
+constexpr int kMaxDevices = 64;        // per-device tables of the host side
+
 int sm_count();                        // SMs of the current device (cached)
 int current_device();
 int cuda_status(cudaError_t e);        // GF_OK or GF_ECUDA (clears sticky-free errors)

@@ -15,10 +15,12 @@
 // The array's host-side name is only a stand-in: its device address is
 // looked up once per device with cudaGetSymbolAddress, on the first call
 // made with that device current.  That first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the
-// last call's contents; the work counter that must start at zero is cleared
-// by every call.  Calls whose work overlaps on the GPU (other streams, other
-// threads) race on the array.
+// before any stream capture.  Each call hands its descriptors to a one-thread
+// set-up kernel as kernel arguments (passed by value, so nothing on the host
+// is read after the call returns); that kernel writes them into the array
+// and clears the work counter that must start at zero.  All calls share the
+// array and it keeps the last call's contents.  Calls whose work overlaps on
+// the GPU (other streams, other threads) race on the array.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -43,13 +45,32 @@ constexpr size_t kNoAllocX = 1024;             // X: n_src x n_recv bytes
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+static_assert(sizeof(WorkCounter) <= kNoAllocDecGen - kNoAllocCounter, "WorkCounter slot");
 static_assert(sizeof(DecGen) <= kNoAllocEncGen - kNoAllocDecGen, "DecGen slot");
 static_assert(sizeof(EncGen) <= kNoAllocTiles - kNoAllocEncGen, "EncGen slot");
+static_assert(2 * sizeof(long long) <= kNoAllocX - kNoAllocTiles, "tile offsets slot");
+
+// The descriptors of one call, passed by value to the set-up kernel.
+struct NoAllocDescs {
+    DecGen dec;
+    EncGen enc;
+    long long tiles[2];
+};
+
+// One thread writes the call's descriptors into the array and clears the
+// payload phase's work counter.
+__global__ void noalloc_setup_kernel(NoAllocDescs d)
+{
+    *reinterpret_cast<DecGen *>(g_noalloc_scratch + kNoAllocDecGen) = d.dec;
+    *reinterpret_cast<EncGen *>(g_noalloc_scratch + kNoAllocEncGen) = d.enc;
+    long long *tiles = reinterpret_cast<long long *>(g_noalloc_scratch + kNoAllocTiles);
+    tiles[0] = d.tiles[0];
+    tiles[1] = d.tiles[1];
+    *reinterpret_cast<WorkCounter *>(g_noalloc_scratch + kNoAllocCounter) = WorkCounter{};
+}
 
 // Device address of the scratch array on the current device (looked up once;
 // a fixed table, so the lookup itself allocates nothing).
-constexpr int kMaxDevices = 64;
-
 static int scratch_address(unsigned char **out)
 {
     static std::mutex mu;
@@ -69,15 +90,6 @@ static int scratch_address(unsigned char **out)
     return GF_OK;
 }
 
-static size_t noalloc_smem_limit()
-{
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device()) != cudaSuccess ||
-        v <= 0)
-        v = 48 * 1024;
-    return (size_t)v - 1024;
-}
-
 }  // namespace gf
 
 using namespace gf;
@@ -95,7 +107,7 @@ extern "C" int gf_decode_noalloc(int field, int n_src, int n_recv, uint64_t len,
     if ((size_t)n_src * (size_t)n_recv > kNoAllocBytes - kNoAllocX) return GF_EINVAL;
     const int W = (int)align_up((size_t)n_src + (size_t)n_recv, 16);
     const size_t smem = dec_smem_bytes(field, n_src, W, true);
-    if (smem > noalloc_smem_limit()) return GF_EINVAL;
+    if (smem > decode_smem_limit()) return GF_EINVAL;
 
     unsigned char *scratch = nullptr;
     int st = scratch_address(&scratch);
@@ -130,14 +142,16 @@ extern "C" int gf_decode_noalloc(int field, int n_src, int n_recv, uint64_t len,
     e.variant = choose_table_variant(field, n_recv, n_src, len);
     const long long tiles[2] = {0, table_tiles_for(e)};
 
-    // descriptors into the array (pageable copies, staged by the driver), counter cleared
-    if (cudaMemcpyAsync(scratch + kNoAllocDecGen, &g, sizeof(g), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(scratch + kNoAllocEncGen, &e, sizeof(e), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(scratch + kNoAllocTiles, tiles, sizeof(tiles), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemsetAsync(scratch + kNoAllocCounter, 0, sizeof(WorkCounter), s) != cudaSuccess) {
-        cudaGetLastError();
-        return GF_ECUDA;
-    }
+    // descriptors into the array and the counter cleared, by a kernel whose
+    // arguments carry them
+    NoAllocDescs d{};
+    d.dec = g;
+    d.enc = e;
+    d.tiles[0] = tiles[0];
+    d.tiles[1] = tiles[1];
+    noalloc_setup_kernel<<<1, 1, 0, s>>>(d);
+    st = cuda_status(cudaGetLastError());
+    if (st != GF_OK) return st;
     st = launch_decode_coef_raw(reinterpret_cast<const DecGen *>(scratch + kNoAllocDecGen), 1, smem, s);
     if (st != GF_OK) return st;
     return launch_table_raw(reinterpret_cast<const EncGen *>(scratch + kNoAllocEncGen),
