@@ -147,44 +147,84 @@ def rank_barrier():
 # ---------------------------------------------------------------------------
 # reference arm / cpu baseline: the oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_encode_rate(batch, budget_s: float, max_gens: int | None = None):
-    """Times the oracle's encode on whole generations until `budget_s` has
-    passed; returns (coded-output GB/s, generations done)."""
+def host_info() -> dict:
+    """Host CPU model (lscpu) and core count, recorded beside every CPU figure."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_encode_round(batch, first: int, threads: int):
+    """Encodes generations first .. first+threads-1 (mod the batch) with the
+    C oracle, one generation per host thread (the oracle's C call releases
+    the GIL); returns the seconds taken."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    n = batch.src.shape[0]
+    idx = [(first + t) % n for t in range(threads)]
+    t0 = time.perf_counter()
+    if threads == 1:
+        oracle.encode(batch.field, batch.src[idx[0]], batch.coef[idx[0]])
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(lambda i: oracle.encode(batch.field, batch.src[i], batch.coef[i]), idx))
+    return time.perf_counter() - t0
+
+
+def oracle_encode_rate(batch, threads: int, budget_s: float, max_gens: int):
+    """Rounds of `threads` generations until `budget_s` seconds have passed or
+    `max_gens` generations are done, whichever comes first; returns
+    (coded-output GB/s, generations done, seconds)."""
     import oracle
     oracle.build()
-    done, t0 = 0, time.perf_counter()
-    n = batch.src.shape[0]
-    while True:
-        i = done % n
-        oracle.encode(8, batch.src[i], batch.coef[i])
-        done += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or (max_gens and done >= max_gens):
-            break
-    out_bytes = done * N_CODED * LEN
-    return out_bytes / el / 1e9, done, el
+    K, L = batch.coef.shape[1], batch.src.shape[2]
+    done, el = 0, 0.0
+    while done < max_gens and el < budget_s:
+        el += oracle_encode_round(batch, done, threads)
+        done += threads
+    return done * K * L / el / 1e9, done, el
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the C oracle on the host cores, on the GPU arm's
+    batch (4096 x 64 x 1500 B, GF(256), K = 64).  A step encodes one round of
+    generations, one per host thread; `ms_per_step` is that round's measured
+    time and the whole batch's time is extrapolated under its own key."""
     if rank != 0:
         return
+    import oracle
     from paper_1909_02871_gb300 import synth
-    batch = synth.uniform_batch(n_gens=16, index=1)
-    for _ in range(args.warmup):
-        oracle_encode_rate(batch, 0.0, max_gens=1)
-    vals = []
-    for _ in range(args.steps):
-        v, done, el = oracle_encode_rate(batch, 0.0, max_gens=2)
-        vals.append(v)
-    value = statistics.median(vals)
-    ms = 2 * N_CODED * LEN / (value * 1e9) * 1e3 * (N_GENS / 2)
+    oracle.build()
+    threads = os.cpu_count() or 1
+    batch = synth.uniform_batch(n_gens=N_GENS, index=0)
+    for w in range(args.warmup):
+        oracle_encode_round(batch, w * threads, threads)
+    times = [oracle_encode_round(batch, (args.warmup + s) * threads, threads) for s in range(args.steps)]
+    total = sum(times)
+    value = args.steps * threads * N_CODED * LEN / total / 1e9
+    ms = total / args.steps * 1e3
+    sample = (f"each step: {threads} generations (64 x 64 x 1500 B, K = 64) of the batch encoded by the C oracle, "
+              f"one generation per host thread, {threads} threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "2 generations per step, extrapolated to 4096"},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "each step: 2 generations (64 x 64 x 1500 B) encoded by the C oracle, "
-                                       "one thread"},
+            "config": {"workload": WORKLOAD, "n_gens": N_GENS, "n_src": N_SRC, "n_coded": N_CODED, "len": LEN,
+                       "field": "GF(256)", "sample": sample},
+            "generations_per_step": threads,
+            "extrapolated_ms_per_batch": ms * N_GENS / threads,
+            "host": host_info(),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -289,40 +329,62 @@ def run_gf(args, rank, world, local_rank):
         line["region_madd"] = bench_region(gf, torch, dev, stream, hbm_peak, peak_kind)
         line["plain"] = bench_plain(gf, torch, dev, stream, src, coef, out, value)
         line["e2e"] = bench_e2e(gf, torch, dev, stream, src_h, coef_h, args, plan, src, coef, out)
-        v, done, el = oracle_encode_rate(batch, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{done} generations of the same batch (64 x 64 x 1500 B) encoded by the "
-                                          f"C oracle in {el:.1f} s, one thread"}
     plan.close()
+    if rank == 0 and not args.quick:
+        del src, coef, out
+        torch.cuda.empty_cache()
+        line["serving"] = serve_leg(torch, dev, args.serve_requests, (0.5,))
+        host = host_info()
+        v, done, el = oracle_encode_rate(batch, 1, args.cpu_seconds, 400)
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "host": host,
+                                "sample": f"{done} generations of the same batch (64 x 64 x 1500 B, K = 64) encoded "
+                                          f"by the C oracle in {el:.1f} s, one thread"}
+        nt = host["nproc"] or 1
+        v, done, el = oracle_encode_rate(batch, nt, args.cpu_seconds, 64 * nt)
+        line["cpu_baseline_all_cores"] = {
+            "value": v, "unit": "GB/s", "cores": nt, "kind": "oracle", "host": host,
+            "sample": f"{done} generations of the same batch encoded by the C oracle in {el:.1f} s, one generation "
+                      f"per thread, {nt} threads"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def bench_region(gf, torch, dev, stream, hbm_peak, peak_kind):
-    """gf_region_madd / gf_region_mul on a 1 GiB region (larger than L2), GF(256)."""
+    """gf_region_madd / gf_region_mul on a 1 GiB region (larger than L2) in
+    every field, against the measured HBM copy bandwidth: 3 bytes moved per
+    region byte for madd, 2 for mul."""
     n = 1 << 30
     g = torch.Generator(device=dev)
     g.manual_seed(5)
     a = torch.randint(0, 256, (n,), dtype=torch.uint8, device=dev, generator=g)
     b = torch.randint(0, 256, (n,), dtype=torch.uint8, device=dev, generator=g)
-    res = {}
+    points = []
+    coefs = {1: 1, 2: 0x2, 4: 0xB, 8: 0x8E}
     with torch.cuda.stream(stream):
-        for name, fn, bytes_per in (("madd", gf.gf_region_madd, 3), ("mul", gf.gf_region_mul, 2)):
-            for _ in range(3):
-                fn(8, b, a, 0x8E, stream=stream)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 10
-            e0.record(stream)
-            for _ in range(reps):
-                fn(8, b, a, 0x8E, stream=stream)
-            e1.record(stream)
-            stream.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            gbs = bytes_per * n / (ms / 1e3) / 1e9
-            res[name] = {"GBps_hbm": gbs, "frac": gbs / hbm_peak, "peak": hbm_peak, "peak_kind": peak_kind,
-                         "ms": ms, "len": n}
+        for field in (1, 2, 4, 8):
+            for name, fn, bytes_per in (("madd", gf.gf_region_madd, 3), ("mul", gf.gf_region_mul, 2)):
+                c = coefs[field]
+                for _ in range(3):
+                    fn(field, b, a, c, stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 10
+                e0.record(stream)
+                for _ in range(reps):
+                    fn(field, b, a, c, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                gbs = bytes_per * n / (ms / 1e3) / 1e9
+                points.append({"field": field, "op": name, "coef": c, "GBps_hbm": gbs, "frac": gbs / hbm_peak,
+                               "ms": ms, "len": n})
     del a, b
     torch.cuda.empty_cache()
+    res = {"points": points, "peak": hbm_peak, "peak_kind": peak_kind,
+           "min_frac": min(p["frac"] for p in points), "launches": len(points) * 13}
+    # the GF(256) points under their old keys
+    for p in points:
+        if p["field"] == 8:
+            res[p["op"]] = {k: p[k] for k in ("GBps_hbm", "frac", "ms", "len")}
     return res
 
 
@@ -381,6 +443,25 @@ def bench_e2e(gf, torch, dev, stream, src_h, coef_h, args, plan, src, coef, out)
            "h2d_bytes_per_step": int(src_h.numel() + coef_h.numel()), "d2h_bytes_per_step": int(out_h.numel()),
            "ms_per_step": ms, "chunks": len(enc.ranges), "gpu_launches_per_step": enc.kernel_count}
     enc.close()
+    # the host link's own bound: the same bytes copied with no encode, the
+    # uploads and downloads on two streams at once
+    up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(up)
+    down.wait_event(e0)
+    for _ in range(steps):
+        with torch.cuda.stream(up):
+            src.copy_(src_h, non_blocking=True)
+            coef.copy_(coef_h, non_blocking=True)
+        with torch.cuda.stream(down):
+            out_h.copy_(out, non_blocking=True)
+    e1.record(up)
+    e2.record(down)
+    torch.cuda.synchronize()
+    link_ms = max(e0.elapsed_time(e1), e0.elapsed_time(e2)) / steps
+    res["copies_only_ms_per_step"] = link_ms
+    res["frac_of_copies_only"] = link_ms / ms
     return res
 
 
@@ -433,6 +514,38 @@ def run_uneven(args, rank, world, local_rank):
     stream.synchronize()
     plain_s = time.perf_counter() - t0
     value = whole_job_rate(work.bytes_src, world, args.steps, total_ms) / 1e9
+    # the two plans of a step timed on their own (outside the graph)
+    part_ms = {}
+    for name, plan in (("encode", step.enc), ("decode", step.dec)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            plan.launch(stream)
+            e0.record(stream)
+            for _ in range(3):
+                plan.launch(stream)
+            e1.record(stream)
+        stream.synchronize()
+        part_ms[name] = e0.elapsed_time(e1) / 3
+    # algorithmic work in the bit-sliced count of the scope table: 2 * 8K * 8N * len FLOP per
+    # generation for the sender's K packets, 2 * 8N * 8R * len for the payload phase of the
+    # decode (N sources from R received packets); the coefficient phase's byte multiply-adds
+    # (about N^2 (N + R) per generation) on the integer ALU are counted apart
+    enc_flop = sum(2.0 * 64 * g.n_src * k * g.length for g, k in zip(batch.gens, work.k_sent))
+    dec_flop = sum(2.0 * 64 * g.n_src * rr.size * g.length for g, rr in zip(batch.gens, work.recv_rows))
+    coef_madds = sum(float(g.n_src) ** 2 * (g.n_src + rr.size) for g, rr in zip(batch.gens, work.recv_rows))
+    _, bf16_peak, peak_kind = _peaks()
+    peak = 6.0 * bf16_peak
+    step_avg = statistics.mean(step_ms)
+    roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+            "peak_kind": f"{peak_kind} bf16 x 6 (fp4 nominal ratio)",
+            "kernel": "whole step: sender encode + decode payload phase in the bit-sliced FLOP count",
+            "achieved": (enc_flop + dec_flop) / (step_avg / 1e3) / 1e12,
+            "encode": {"flop": enc_flop, "ms": part_ms["encode"],
+                       "achieved": enc_flop / (part_ms["encode"] / 1e3) / 1e12},
+            "decode": {"payload_flop": dec_flop, "coef_phase_byte_madds": coef_madds, "ms": part_ms["decode"]},
+            "traffic": None}
+    roof["frac"] = roof["achieved"] / peak
+    roof["encode"]["frac"] = roof["encode"]["achieved"] / peak
     line = {"metric": "uneven encode+decode GB/s (source bytes per step)", "value": value, "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -441,7 +554,7 @@ def run_uneven(args, rank, world, local_rank):
                        "source_bytes": work.bytes_src, "coded_bytes": work.bytes_coded,
                        "packets_sent": int(sum(work.k_sent))},
             "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
-            "gpu_launches": step.kernel_count * args.steps, "clocks": clk.summary(),
+            "gpu_launches": step.kernel_count * args.steps, "clocks": clk.summary(), "roofline": roof,
             "round_trip_ok": not bad,
             "plain": {"value": sub_bytes / plain_s / 1e9, "unit": "GB/s",
                       "sample": f"{len(sub)} generations, one encode + one decode call each, host wall time"}}
@@ -450,18 +563,13 @@ def run_uneven(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def run_serve(args, rank, world, local_rank):
-    """Serving: Poisson arrivals of encode and decode requests (shapes of the
-    uneven workload), admitted by device memory, decode packets arriving one
-    by one; throughput and p50/p99 latency at several arrival rates."""
-    import torch
-
+def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30) -> dict:
+    """Serving: n requests (half encode, half decode) with the uneven
+    workload's shapes; saturation throughput (every request arriving at once)
+    and, for each fraction f of it, Poisson arrivals at f x saturation with
+    decode packets arriving 20 us apart: p50/p99 request latency.  Decoded
+    results are checked against the sources."""
     from paper_1909_02871_gb300 import gf, serve, synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    gf.load()
-    n = args.requests
     batch = synth.uneven_batch(n_gens=n, index=7)
     # coded packets of the decode requests, produced by the library (untimed)
     coded = {}
@@ -492,37 +600,64 @@ def run_serve(args, rank, world, local_rank):
                                                float(t) + gap * np.arange(1, c.shape[0] + 1)))
         return out
 
-    budget = 4 << 30
-    # saturation: everything arrives at once
-    reqs = requests(np.zeros(n), 0.0)
-    serve.Server(mem_budget=budget).run(reqs[:32])  # warm-up
+    def ok(reqs):
+        return all(np.array_equal(r.result, batch.gens[r.rid].src) for r in reqs
+                   if isinstance(r, serve.DecodeRequest))
+
+    serve.Server(mem_budget=budget).run(requests(np.zeros(n), 0.0)[:32])  # warm-up
     reqs = requests(np.zeros(n), 0.0)
     srv = serve.Server(mem_budget=budget)
-    rank_barrier()
-    wall = max_over_ranks(srv.run(reqs), dev)
-    sat = whole_job_rate(n, world, 1, wall * 1e3)  # every rank serves its own n requests
-    ok = all(np.array_equal(r.result, batch.gens[r.rid].src) for r in reqs if isinstance(r, serve.DecodeRequest))
-    plain_reqs = requests(np.zeros(n), 0.0)[:64]
-    plain_wall = serve.Server(mem_budget=budget, max_active=1).run(plain_reqs)
+    wall = srv.run(reqs)
+    sat = n / wall
+    good = ok(reqs)
+    launches = srv.launches
     rates = {}
-    for f in (0.25, 0.5, 0.9):
+    for f in fractions:
         rate = f * sat
         r2 = requests(synth.arrivals(rate, n, index=int(f * 100)), 20e-6)
         s2 = serve.Server(mem_budget=budget)
         w2 = s2.run(r2)
+        good = good and ok(r2)
         st = serve.latency_stats(r2)
         st.update({"rate_req_per_s": rate, "throughput_req_per_s": n / w2, "batches": s2.batches})
         rates[f"{f:.2f}x"] = st
-    total_bytes = sum(ge.src.size for ge in batch.gens)
+        launches += s2.launches
+    return {"requests": n, "saturation_req_per_s": sat, "saturation_wall_s": wall,
+            "source_bytes": int(sum(ge.src.size for ge in batch.gens)), "rates": rates, "round_trip_ok": good,
+            "gpu_launches": launches, "device_memory_budget": budget,
+            "workload": f"{n} requests, half encode (K = N) and half decode, uneven shapes (N ~ U{{8..255}}, len "
+                        "log-uniform 64-9000 B, four fields), decode packets 20 us apart"}
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving: Poisson arrivals of encode and decode requests (shapes of the
+    uneven workload), admitted by device memory, decode packets arriving one
+    by one; throughput and p50/p99 latency at several arrival rates."""
+    import torch
+
+    from paper_1909_02871_gb300 import gf, serve, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gf.load()
+    n = args.requests
+    rank_barrier()
+    with Clocks(local_rank) as clk:
+        leg = serve_leg(torch, dev, n, (0.25, 0.5, 0.9))
+    sat = whole_job_rate(n, world, 1, max_over_ranks(leg["saturation_wall_s"], dev) * 1e3)
+    # the plain form: one request at a time
+    batch = synth.uneven_batch(n_gens=64, index=7)
+    plain_reqs = [serve.EncodeRequest(i, 0.0, ge.field, ge.src, np.ascontiguousarray(ge.coef_stream[:ge.n_src]))
+                  for i, ge in enumerate(batch.gens)]
+    plain_wall = serve.Server(max_active=1).run(plain_reqs)
     line = {"metric": "serving throughput req/s and p99 ms", "value": sat, "unit": "req/s", "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"serving: {n} requests (half encode, half decode), shapes of the uneven "
-                                   "workload, Poisson arrivals, decode packets 20 us apart",
-                       "device_memory_budget": budget, "source_bytes": total_bytes},
-            "saturation_GBps_source": total_bytes / wall / 1e9, "rates": rates,
-            "plain_req_per_s": len(plain_reqs) / plain_wall, "round_trip_ok": ok,
-            "gpu_launches": srv.launches}
+            "steps": 1, "warmup": 1, "ms_per_step": leg["saturation_wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serving: " + leg["workload"] + ", Poisson arrivals",
+                       "device_memory_budget": leg["device_memory_budget"], "source_bytes": leg["source_bytes"]},
+            "saturation_GBps_source": leg["source_bytes"] / leg["saturation_wall_s"] / 1e9, "rates": leg["rates"],
+            "plain_encode_req_per_s": len(plain_reqs) / plain_wall, "round_trip_ok": leg["round_trip_ok"],
+            "clocks": clk.summary(), "gpu_launches": leg["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -784,6 +919,7 @@ def main():
     ap.add_argument("--path", choices=["auto", "table", "bitsliced"], default="auto")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests of the default line's serving leg")
     ap.add_argument("--region-min-log", type=int, default=10, help="region sweep: smallest size 2^k bytes")
     ap.add_argument("--region-fields", type=int, nargs="+", default=[1, 2, 4, 8], help="region sweep: fields")
     ap.add_argument("--uniform-gens", type=int, default=None,
