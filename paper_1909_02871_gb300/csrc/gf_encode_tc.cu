@@ -14,32 +14,48 @@
 // (Eq. 2 is a sum over sources).  The operands are
 // E2M1 (4-bit) values 0 and 1.0 with every block scale 1.0 (UE8M0 127),
 // which runs at twice the FP8 rate.  The kernel computes the product
-// transposed, one 128-byte column tile at a time:
-//     D[l, 8k'+r] = 2^23 + sum_{(i,j)} A[l, 8i+j] * B[8i+j, 8k'+r]
+// transposed, one 128-byte column tile at a time, two coded packets per
+// accumulator column:
+//     D[l, 8p+r] = 2^23 + S_lo + 2^10 * S_hi,
+//     S_lo = sum_{(i,j)} A[l, 8i+j] * B_lo[8i+j, 8p+r]   (packet p of the item)
+//     S_hi = sum_{(i,j)} A[l, 8i+j] * B_hi[8i+j, 8p+r]   (packet p + 32)
 //   A (M = 128 byte positions x K = 8N source bits): written by the producer
 //     warps straight into tensor memory with tcgen05.st (one TMEM lane per
 //     byte position, one column = the 8 bit values of one source byte);
-//   B (K = 8N x N = 256 output bits of 32 coded packets): the coefficients'
-//     bit matrices, K-major, 128-byte swizzled, two halves of 64 KB in shared
-//     memory (64 sources; coded packets 0..31 and 32..63 of the item), built
-//     from a per-CTA table of the 8x8 blocks of every coefficient;
-//   D (128 lanes x 256 FP32 columns): one N = 256 MMA stream per tile.  The
-//     first MMA of a tile is a rank-1 product with block scale 2^23 that sets
-//     every element to 2^23; the sum then sits in the low mantissa bits
-//     (exact: ulp(2^23) = 1), so the epilogue reads only the low 16 bits of
-//     each column (tcgen05.ld .pack::16b, two columns per register), takes
-//     bit 0 of each of the 8 values of a coded byte and packs them.
+//   B (K = 2 x 8N: the bit matrices of packets 0..31 of the item, then those
+//     of packets 32..63, x N = 256 columns): K-major, 128-byte swizzled, two
+//     halves of 64 KB in shared memory (64 sources each; the lo and the hi
+//     packets), built from a per-CTA table of the 8x8 blocks of every
+//     coefficient.  The MMAs over the hi half reuse the same A columns and
+//     take block scale 2^10 for B (UE8M0 137);
+//   D (128 lanes x 256 FP32 columns): one pass of 17 MMAs (N = 256) covers
+//     all 64 coded packets of the item.  (An MMA costs about 95 SM clocks
+//     whatever its N up to 128 and about 138 at N = 256, so N = 256 with two
+//     packets per column beats double-buffered N = 128 accumulators.)  The
+//     first MMA of a pass is a rank-1 product with block scale 2^23 that
+//     sets every element to 2^23, so both sums sit in the low mantissa bits
+//     (exact: every value is an integer below 2^24, ulp(2^23) = 1).  A sum
+//     is at most 512 < 2^10, so the parity of S_lo is bit 0 and that of S_hi
+//     is bit 10; the epilogue reads only the low 16 bits of each column
+//     (tcgen05.ld .pack::16b, two columns per register) and packs the 8 bits
+//     of each coded byte.  An item of at most 32 coded packets skips the
+//     hi half (its build and its MMAs).
 // Work item = (generation, up to 64 coded packets); the CTA loops over the
 // item's 64-source chunks and, within each, over all column tiles; each A
-// tile feeds one D pass per half (so the source bit planes are built once
-// per 64 coded packets).  The first chunk's passes write the coded bytes,
+// tile feeds one D pass (so the source bit planes are built once per 64
+// coded packets).  The first chunk's passes write the coded bytes,
 // later chunks' passes XOR into them (the same thread owns the same bytes).  Roles, all running
 // concurrently: 4 warps publish the next item in a two-entry ring and build
 // each half of its B as soon as the previous item's last pass over that half
 // is done; 8 producer warps stage their source rows in shared memory with
 // cp.async two tiles ahead and fill A (double-buffered in TMEM, via a 1 KB
-// table of pre-spread words); 1 warp issues the MMAs (converged, one
-// elected lane issues); 16 epilogue warps drain D.  Handshakes arrive once per warp
+// bit spread computed in registers); 1 warp issues the MMAs (converged, one
+// elected lane issues; an MMA's issue holds the warp until the tensor pipe
+// takes it, so the warp does nothing else); 16 epilogue warps drain D and
+// release each A buffer once the D of its pass has landed; the B builders
+// rebuild each half for the next item as soon as the MMAs of the item's
+// last pass over that half are complete (a commit between the lo and the
+// hi MMAs).  Handshakes arrive once per warp
 // (after __syncwarp).  A role of several warps waits through one polling
 // warp while the others are parked on a named barrier, which also hands
 // every warp the same outcome.  Every mbarrier wait is bounded by the global
@@ -65,7 +81,8 @@ constexpr int kBWarp0 = kMmaWarp + 1;                       // warps 25..28
 constexpr int kThreads = (kProducerWarps + kEpilogueWarps + 1 + kBWarps) * 32;  // 928
 constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerItem = 64;   // coded packets per work item: two halves
-constexpr int kCodedPerHalf = 32;   // coded packets per D pass (MMA N = 256 output bits)
+constexpr int kCodedPerHalf = 32;   // coded packets of one B half (lo: bit 0, hi: bit 10 of the sums)
+constexpr int kDN = 256;            // MMA N: accumulator columns per pass (32 packet slots x 8 bits)
 constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: 64 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
@@ -73,32 +90,31 @@ constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte posit
 // tensor memory columns (all 512 allocated)
 constexpr int kTmemCols = 512;
 constexpr int kABufCols = 64;       // A buffers at columns 0 and 64 (one column per source)
-constexpr int kBiasACol = 128;      // rank-1 bias operand: element 0 = 1.0, 8 columns
+constexpr int kBiasACol = 128;      // rank-1 bias operand: element 0 = 1.0, 16 columns
+constexpr int kSfHiB = 144;         // block scales 2^10 (UE8M0 137) for B of packets 16..31, 16 columns
 constexpr int kSfOneA = 160;        // block scales 1.0 (UE8M0 127) for A, 32 columns
 constexpr int kSfOneB = 192;        // block scales 1.0 for B, 32 columns
 constexpr int kSfBiasA = 224;       // block scales 2^23 (UE8M0 150) for the bias MMA, 32 columns
 constexpr int kDCol0 = 256;         // D: 256 columns from column 256
 constexpr uint32_t kOne = 0x2u;     // 1.0 in E2M1
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;   // four UE8M0 scales 2^0
+constexpr uint32_t kScaleHi = 0x89898989u;    // four UE8M0 scales 2^10
 constexpr uint32_t kScaleBias = 0x96969696u;  // four UE8M0 scales 2^23
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s per wait
-constexpr uint32_t kSuspendNs = 100000;                 // try_wait suspend hint
 constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
-constexpr int kKBlock = 256 * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
-constexpr int kBBytes = 2 * kKBlock;        // 64 KB: B of one half item (K <= 512)
+constexpr int kKBlock = kDN * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
+constexpr int kBBytes = 2 * kKBlock;        // 64 KB: one B half (K <= 512, 32 coded packets)
 constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
 // 8x8 E2M1 blocks of every coefficient of GF(256), GF(16), GF(4), GF(2):
-// row r of the block of c in field GF(2^n) is word r * 256 + base(n) + c,
-// GF(256) in rows 0..7, the small fields side by side in rows 8..15
+// row r of the block of c in field GF(2^n) is word 8 * (base(n) + c) + r
+// (one 32-byte block per coefficient, read with two 16-byte loads)
 constexpr int kTabBase8 = 0, kTabBase4 = 8 * 256, kTabBase2 = 8 * 256 + 16, kTabBase1 = 8 * 256 + 16 + 4;
 constexpr int kTabRow = 256;
 constexpr int kTabBytes = 16 * 1024;
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
-constexpr int kSpreadBytes = 256 * 4;       // 1 KB: the 8 E2M1 bit values of every source byte
-constexpr int kSmemBytes =
-    2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + kSpreadBytes + 1024 /*control*/ + 1024 /*slack*/;
+constexpr int kSmemBytes = 2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*slack*/;
 
 struct Ctl {
     unsigned long long a_full[2], a_empty[2], d_full, d_empty;
@@ -135,10 +151,10 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *bar, uint32_t parit
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+        : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
@@ -272,16 +288,19 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
 // Instruction descriptor, kind::mxf4 block-scaled: A = B = E2M1 (format 1),
 // both K-major, N = 256, scale type UE8M0 (bit 23), M = 128, scale-factor
 // ids 0, dense K = 64.  D is FP32.
-constexpr uint32_t kIdesc = (0u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) | (1u << 23) |
+constexpr uint32_t kIdesc = (0u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kDN >> 3) << 17) | (1u << 23) |
                             ((uint32_t)(128 >> 4) << 24);
 
-// the 8 E2M1 values (nibbles j = 0..7) of one source byte: 1.0 where bit j is set
-__host__ __device__ __forceinline__ uint32_t spread_bits(uint32_t b)
+// the 8 E2M1 values (nibbles j = 0..7) of one source byte: 1.0 (0x2) where
+// bit j is set.  Bit j moves to bit 4j + 1 in three halving steps (nibbles
+// apart, then bit pairs, then bits), without a table lookup: shared-memory
+// lookups here contended with the tensor core's operand reads.
+__device__ __forceinline__ uint32_t spread_bits(uint32_t b)
 {
-    uint32_t w = 0;
-    for (int j = 0; j < 8; ++j)
-        if ((b >> j) & 1u) w |= kOne << (4 * j);
-    return w;
+    uint32_t x = (b | (b << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
 }
 
 // parity byte of 8 biased sums, low 16 bits packed two per word (word j =
@@ -294,6 +313,15 @@ __device__ __forceinline__ uint32_t parity_byte(const uint32_t *v)
 {
     const uint32_t q0 = prmt(v[0], v[1], 0x6420u) & 0x01010101u;
     const uint32_t q1 = prmt(v[2], v[3], 0x6420u) & 0x01010101u;
+    return ((q1 * 16u + q0) * 0x01020408u) >> 24;
+}
+
+// The same for bit 10 of each half (bit 2 of its high byte): the parities
+// of the sums weighted 2^10.
+__device__ __forceinline__ uint32_t parity_byte_hi(const uint32_t *v)
+{
+    const uint32_t q0 = (prmt(v[0], v[1], 0x7531u) >> 2) & 0x01010101u;
+    const uint32_t q1 = (prmt(v[2], v[3], 0x7531u) >> 2) & 0x01010101u;
     return ((q1 * 16u + q0) * 0x01020408u) >> 24;
 }
 
@@ -389,8 +417,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     unsigned char *bias_b = smem + 2 * kBBytes;
     uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][field][c]
     unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
-    uint32_t *spread = reinterpret_cast<uint32_t *>(staging + kStageAll);  // [source byte]
-    Ctl *ctl = reinterpret_cast<Ctl *>(reinterpret_cast<unsigned char *>(spread) + kSpreadBytes);
+    Ctl *ctl = reinterpret_cast<Ctl *>(staging + kStageAll);
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
@@ -401,8 +428,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     // the same c, so the block is block-diagonal: output bit r (word r/n,
     // bit r%n), input bit j (word j/n, bit j%n) is bit r%n of c*x^(j%n)
     // when both lie in the same word.  Row r is one word, nibble j = that
-    // bit; tables are [r][c] so that lanes looking up different
-    // coefficients for the same row spread over the shared-memory banks.
+    // bit; a coefficient's 8 rows are contiguous (one 32-byte block).
     for (int e = tid; e < 8 * 256; e += blockDim.x) {
         const uint32_t c = (uint32_t)e & 255u, r = (uint32_t)e >> 8;
         uint32_t p = c, row = 0;
@@ -426,7 +452,6 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             tab[kTabBase4 + r * kTabRow + col] = row;
         }
     }
-    for (int v = tid; v < 256; v += blockDim.x) spread[v] = spread_bits((uint32_t)v);
     // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
     for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x) {
         const int n = e >> 3, phys = e & 7;
@@ -469,6 +494,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         for (int j = 0; j < 16; ++j) v[j] = 0u;
         v[0] = kOne;
         tmem_st16(q + kBiasACol, v);
+        tmem_fill16(q + kSfHiB, kScaleHi);
         for (int c = 0; c < 32; c += 16) {
             tmem_fill16(q + kSfOneA + c, kScaleOne);
             tmem_fill16(q + kSfOneB + c, kScaleOne);
@@ -553,7 +579,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 if (kb < nkb) {
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int kp = kq * 4 + t;
+                        const int kp = kq * 4 + t;  // packet of the half = column slot
                         const uint32_t w = cc[t];
 #pragma unroll
                         for (int r = 0; r < 8; ++r) {
@@ -655,7 +681,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                                         b, 2 * half + grp);
                         }
 #pragma unroll
-                        for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread[b[t]];
+                        for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread_bits(b[t]);
                     }
                     tmem_st16(acol + half * 16, v);
                 }
@@ -670,8 +696,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         }
     } else if (warp < kProducerWarps + kEpilogueWarps) {
         // ---------------- epilogue: 64 D columns -> parity bytes -> global ----------------
+        // warp (quarter, oct) drains packet slots 8 oct .. 8 oct + 7 of its lane quarter: coded
+        // packets 8 oct + t (bit 0 of the sums) and 32 + 8 oct + t (bit 10) of the item
         const int quarter = warp & 3;
-        const int oct = (warp - kProducerWarps) >> 2;   // 8-packet group of the item: 0..3
+        const int oct = (warp - kProducerWarps) >> 2;   // 8-slot group: 0..3
         const int pos = quarter * 32 + lane;
         const bool poller = warp == kProducerWarps;
         uint32_t tiles = 0;
@@ -691,21 +719,21 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const unsigned long long len = g.len;
-            const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
+            const int klo = k0i + oct * 8, khi = klo + kCodedPerHalf;  // first packet of each group of 8
+            const int nlo = min(8, g.n_coded - klo), nhi = min(8, g.n_coded - khi);  // live packets
             bool ok = true;
-            for (int pass = 0; pass < nunits * nh; ++pass) {
-                const int v = nh == 2 ? pass >> 1 : pass, h = nh == 2 ? pass & 1 : 0;
+            for (int v = 0; v < nunits; ++v) {
                 const bool first = v < ncols;  // source chunk 0 writes, later chunks add (XOR) their share
                 const int ct = first ? v : v % ncols;
-                const int k0 = k0i + h * kCodedPerHalf + oct * 8;
-                const int nk = min(8, g.n_coded - k0);          // live coded packets of this warp
                 if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                // the MMAs of this unit's pass are complete: its A buffer is free
+                if (poller && lane == 0) mbar_arrive(&ctl->a_empty[tiles & 1u]);
                 const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + oct * 64;
                 uint32_t va[16], vb[16];
                 tmem_ld16_pack(dcol, va);
@@ -714,32 +742,54 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ctl->d_empty);  // D is free as soon as it is in registers
-                uint32_t outb[8];
+                // the 16 output bytes, four per register: lo packets 0..3, 4..7, hi packets 0..3, 4..7
+                uint32_t ob[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    outb[t] = parity_byte(va + 4 * t);
-                    outb[4 + t] = parity_byte(vb + 4 * t);
-                }
-                if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nk > 0) {
-                    uint8_t *o = g.out + (size_t)k0 * len + (size_t)(c0 + ct) * kColTile + pos;
-                    if (first) {
-#pragma unroll
-                        for (int kp = 0; kp < 8; ++kp) {
-                            if (kp < nk) *o = (uint8_t)outb[kp];
-                            o += len;
-                        }
+                    const uint32_t l0 = parity_byte(va + 4 * t), l1 = parity_byte(vb + 4 * t);
+                    const uint32_t h0 = parity_byte_hi(va + 4 * t), h1 = parity_byte_hi(vb + 4 * t);
+                    if (t == 0) {
+                        ob[0] = l0; ob[1] = l1; ob[2] = h0; ob[3] = h1;
                     } else {
-                        // a later source chunk adds its share to the bytes this thread wrote for the
-                        // earlier chunks (same lane, same packets); all eight loads are issued before
-                        // any store (a load after a store through the same pointer type would
-                        // otherwise wait for the previous byte's round trip)
-                        uint32_t prev[8];
+                        ob[0] |= l0 << (8 * t); ob[1] |= l1 << (8 * t);
+                        ob[2] |= h0 << (8 * t); ob[3] |= h1 << (8 * t);
+                    }
+                }
+                if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nlo > 0) {
+                    // two groups of 8 packets (lo, hi), one pointer walked down each group's rows
 #pragma unroll
-                        for (int kp = 0; kp < 8; ++kp) prev[kp] = kp < nk ? (uint32_t)o[(size_t)kp * len] : 0u;
+                    for (int grp = 0; grp < 2; ++grp) {
+                        const int nk = grp ? nhi : nlo;
+                        if (nk <= 0) break;
+                        uint8_t *o = g.out + (size_t)(grp ? khi : klo) * len + (size_t)(c0 + ct) * kColTile + pos;
+                        const uint32_t w0 = ob[2 * grp], w1 = ob[2 * grp + 1];
+                        if (first) {
 #pragma unroll
-                        for (int kp = 0; kp < 8; ++kp) {
-                            if (kp < nk) *o = (uint8_t)(prev[kp] ^ outb[kp]);
-                            o += len;
+                            for (int t = 0; t < 8; ++t) {
+                                if (t < nk) *o = (uint8_t)((t < 4 ? w0 : w1) >> (8 * (t & 3)));
+                                o += len;
+                            }
+                        } else {
+                            // a later source chunk adds its share to the bytes this thread wrote for
+                            // the earlier chunks (same lane, same packets); the group's eight loads
+                            // are issued before any store (a load after a store through the same
+                            // pointer type would otherwise wait for the previous byte's round trip)
+                            uint32_t p0 = 0u, p1 = 0u;
+                            const uint8_t *q = o;
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const uint32_t b = t < nk ? (uint32_t)*q : 0u;
+                                if (t < 4) p0 |= b << (8 * t);
+                                else p1 |= b << (8 * (t - 4));
+                                q += len;
+                            }
+                            p0 ^= w0;
+                            p1 ^= w1;
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                if (t < nk) *o = (uint8_t)((t < 4 ? p0 : p1) >> (8 * (t & 3)));
+                                o += len;
+                            }
                         }
                     }
                 }
@@ -750,14 +800,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     } else {
         // ---------------- MMA issuer (warp kMmaWarp; one elected lane issues) ----------------
         // The whole warp runs the loop and waits together (a lone looping lane whose
-        // warp-mates sit at the final __syncthreads issues markedly slower).
+        // warp-mates sit at the final __syncthreads issues markedly slower).  One pass per
+        // unit: the bias MMA, the lo MMAs (B half 0), the hi MMAs (B half 1, block scale
+        // 2^10).  A buffers are released by the epilogue once the pass's D has landed.
         uint32_t fills = 0, tiles = 0;
         uint32_t bused0 = 0, bused1 = 0;  // fills of each B half consumed so far
-        // A buffer whose last pass was the previous pass: released by a plain arrival once
-        // the next pass's d_empty wait shows that the epilogue has read that pass's D (so
-        // its MMAs are complete); a tcgen05.commit with MMAs in flight stalls this warp
-        int release_a = -1;
         const uint64_t bias_desc = b_desc(smem_u32(bias_b));
+        const uint64_t bdesc_lo = b_desc(smem_u32(Bs)), bdesc_hi = b_desc(smem_u32(Bs + kBBytes));
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (!warp_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
@@ -772,58 +821,60 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
-            const int nh = (min(kCodedPerItem, g.n_coded - k0i) + kCodedPerHalf - 1) / kCodedPerHalf;
+            const bool hi = g.n_coded - k0i > kCodedPerHalf;  // the item has packets in the hi half
             bool ok = true;
+            int ct = 0, i0 = 0;  // column tile, first source of the 64-source chunk
             for (int v = 0; v < nunits && ok; ++v) {
-                const int kc = v / ncols, ct = v - kc * ncols;  // 64-source chunk, column tile
-                const int ksteps = (min(kMaxSrc, g.n_src - kc * kMaxSrc) + 7) / 8;  // 8 sources per MMA
+                const int ksteps = (min(kMaxSrc, g.n_src - i0) + 7) / 8;  // 8 sources per MMA
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
-                if (!warp_wait(&ctl->a_full[buf], fu & 1u, abort_flag)) {
+                // each source chunk's B halves are built anew, so they are waited for at its first tile
+                if (!warp_wait(&ctl->a_full[buf], fu & 1u, abort_flag) ||
+                    (ct == 0 && !warp_wait(&ctl->b_full[0], bused0 & 1u, abort_flag)) ||
+                    !warp_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
+                tc_fence_after();
                 const uint32_t at = tmem + buf * kABufCols;
-                // the A tile serves both halves of the item: one D pass per 32 coded packets (each
-                // source chunk's B halves are built anew, so they are waited for at its first tile)
-                for (int h = 0; h < nh; ++h) {
-                    if (ct == 0 && !warp_wait(&ctl->b_full[h], (h ? bused1 : bused0) & 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    if (!warp_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    if (release_a >= 0) {
-                        if (lane == 0) mbar_arrive(&ctl->a_empty[release_a]);
-                        release_a = -1;
-                    }
-                    tc_fence_after();
-                    {
-                        // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit
-                        // field: B lies below 256 KB of shared memory)
-                        const uint64_t bdesc0 = b_desc(smem_u32(Bs + h * kBBytes));
-                        const uint32_t dt = tmem + kDCol0;
-                        tc_mma_warp(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
+                const uint32_t dt = tmem + kDCol0;
+                // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field: B
+                // lies below 256 KB of shared memory)
+                tc_mma_warp(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) {
-                            if (s < ksteps)
-                                tc_mma_warp(dt, at + s * 8,
-                                            bdesc0 + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
-                                            tmem + kSfOneA, tmem + kSfOneB, 1u);
-                        }
-                        tc_commit_warp(&ctl->d_full);
-                        if (ct == ncols - 1) tc_commit_warp(&ctl->b_empty[h]);  // this half of B is free for the next item
-                    }
-                    if (ct == ncols - 1) {
-                        if (h) ++bused1;
-                        else ++bused0;
-                    }
-                    ++tiles;
+                for (int s = 0; s < 8; ++s) {
+                    if (s < ksteps)
+                        tc_mma_warp(dt, at + s * 8, bdesc_lo + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4),
+                                    kIdesc, tmem + kSfOneA, tmem + kSfOneB, 1u);
                 }
-                if (!ok) break;
-                release_a = (int)buf;
+                if (ct == ncols - 1) {
+                    tc_commit_warp(&ctl->b_empty[0]);  // the lo half is free for the next item
+                    ++bused0;
+                }
+                if (hi) {
+                    if (ct == 0 && !warp_wait(&ctl->b_full[1], bused1 & 1u, abort_flag)) {
+                        tc_commit_warp(&ctl->d_full);  // the epilogue still sees this pass complete
+                        ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int s = 0; s < 8; ++s) {
+                        if (s < ksteps)
+                            tc_mma_warp(dt, at + s * 8,
+                                        bdesc_hi + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
+                                        tmem + kSfOneA, tmem + kSfHiB, 1u);
+                    }
+                }
+                tc_commit_warp(&ctl->d_full);
+                if (hi && ct == ncols - 1) {
+                    tc_commit_warp(&ctl->b_empty[1]);  // the hi half is free for the next item
+                    ++bused1;
+                }
+                ++tiles;
                 ++fills;
+                if (++ct == ncols) {
+                    ct = 0;
+                    i0 += kMaxSrc;
+                }
             }
             if (!ok) {
                 ctl->abort = 1;

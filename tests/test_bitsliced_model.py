@@ -100,3 +100,62 @@ def test_fp32_sums_above_the_bias_are_exact():
     for _ in range(512):
         acc = np.float32(acc + np.float32(1.0))
     assert int(np.array(acc, dtype=np.float32).view(np.uint32)) & 0xFFFF == 512
+
+
+def test_two_packets_per_fp32_column_are_exact():
+    """Two coded packets share one FP32 accumulator column: the products of
+    packet p's bit matrix are summed with weight 1 and those of packet p + 16
+    with weight 2^10 (a block scale), above the 2^23 bias.  Each sum is at
+    most 512 < 2^10, so the total stays an integer below 2^24 (exact in FP32
+    whatever the order of the K = 64 partial sums), bit 0 is the parity of
+    the first sum and bit 10 that of the second, both in the low 16 bits."""
+    g = synth.choice(33, 0)
+    for trial in range(300):
+        lo = g.integers(0, 2, size=512)
+        hi = g.integers(0, 2, size=512)
+        if trial == 0:
+            lo[:] = 1
+            hi[:] = 1
+        # one partial sum per K = 64 MMA, weight 1 for the first eight, 2^10 for the next eight
+        parts = [np.float32(lo[64 * s:64 * s + 64].sum()) for s in range(8)]
+        parts += [np.float32(1024.0) * np.float32(hi[64 * s:64 * s + 64].sum()) for s in range(8)]
+        acc = np.float32(2.0 ** 23)
+        for s in g.permutation(16):
+            acc = np.float32(acc + parts[s])
+        word = int(np.array(acc, dtype=np.float32).view(np.uint32))
+        assert word - 0x4B000000 == int(lo.sum()) + 1024 * int(hi.sum())
+        assert (word & 1) == (lo.sum() & 1) and ((word >> 10) & 1) == (hi.sum() & 1)
+        assert ((word & 0xFFFF) >> 10) & 1 == (hi.sum() & 1)
+
+
+@pytest.mark.parametrize("n", FIELDS)
+def test_encode_with_two_packets_per_column(n):
+    """Eq. 2 for a pass of 32 coded packets computed as 128 accumulator
+    columns (column 8p + r: bit r of packets p and p + 16), each the FP32
+    value 2^23 + S_lo + 2^10 S_hi, with the parities read from bits 0 and 10;
+    64-source chunks XORed as the kernel does."""
+    g = synth.choice(34, n)
+    N, K, L = 100, 29, 41  # two source chunks, a pass with 13 packets in its second 16
+    src = synth.random_bytes(g, (N, L))
+    coef = synth.coefficients(g, n, (K, N), nonzero=False)
+    mats = {c: bit_matrix(n, c) for c in range(1 << n)}
+    A = bits(src).transpose(0, 2, 1).reshape(8 * N, L)
+    out_bits = np.zeros((32, 8, L), dtype=np.int64)
+    for i0 in range(0, N, 64):
+        i1 = min(N, i0 + 64)
+        Ac = A[8 * i0:8 * i1]
+        B = np.zeros((2, 128, 8 * (i1 - i0)), dtype=np.int64)  # [lo/hi][column][K]
+        for kp in range(32):
+            if kp >= K:
+                continue
+            half, slot = divmod(kp, 16)
+            for i in range(i0, i1):
+                B[half, 8 * slot:8 * slot + 8, 8 * (i - i0):8 * (i - i0) + 8] = mats[int(coef[kp, i])]
+        D = (np.float32(2.0 ** 23) + (B[0] @ Ac).astype(np.float32)
+             + np.float32(1024.0) * (B[1] @ Ac).astype(np.float32)).astype(np.float32)
+        word = D.view(np.uint32).astype(np.int64) & 0xFFFF
+        for kp in range(32):
+            half, slot = divmod(kp, 16)
+            out_bits[kp] ^= (word[8 * slot:8 * slot + 8] >> (10 * half)) & 1
+    out = (out_bits[:K] << np.arange(8)[None, :, None]).sum(axis=1).astype(np.uint8)
+    assert np.array_equal(out, oracle.encode(n, src, coef))
