@@ -563,26 +563,38 @@ def run_uneven(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30) -> dict:
+def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30, systematic: bool = False, loss: float = 0.1,
+              redundancy: float = 0.0, rate_base: float | None = None) -> dict:
     """Serving: n requests (half encode, half decode) with the uneven
     workload's shapes; saturation throughput (every request arriving at once)
-    and, for each fraction f of it, Poisson arrivals at f x saturation with
-    decode packets arriving 20 us apart: p50/p99 request latency.  Decoded
-    results are checked against the sources."""
+    and, for each fraction f, Poisson arrivals at f x rate_base (default: this
+    run's saturation) with decode packets arriving 20 us apart: p50/p99
+    request latency.  An encode request makes N + ceil(redundancy N) packets;
+    a decode request receives a stream with i.i.d. losses `loss`.  With
+    `systematic` the senders send the N sources uncoded first.  Every result is
+    checked: decoded sources against the sources, encode results against a
+    batched encode of the same packets."""
     from paper_1909_02871_gb300 import gf, serve, synth
-    batch = synth.uneven_batch(n_gens=n, index=7)
+    batch = synth.uneven_batch(n_gens=n, index=7, loss=loss)
     # coded packets of the decode requests, produced by the library (untimed)
-    coded = {}
+    coded, rows = {}, {}
     items, keep = [], []
     for i, ge in enumerate(batch.gens):
         if i % 2 == 1:
-            c = np.ascontiguousarray(ge.coef_stream[~ge.erased])
+            if systematic:
+                stream = synth.systematic_stream(ge.coef_stream)
+                c = np.ascontiguousarray(stream[~synth.erasures(stream.shape[0], loss, 7, i)])
+            else:
+                c = np.ascontiguousarray(ge.coef_stream[~ge.erased])
             s_d = torch.from_numpy(ge.src).to(dev)
             c_d = torch.from_numpy(c).to(dev)
             o_d = torch.empty((c.shape[0], ge.length), dtype=torch.uint8, device=dev)
             keep.append((s_d, c_d, o_d))
             items.append((ge.field, ge.n_src, c.shape[0], ge.length, s_d, c_d, o_d))
             coded[i] = (c, o_d)
+        else:
+            extra = int(np.ceil(redundancy * ge.n_src))
+            rows[i] = np.ascontiguousarray(ge.coef_stream[:extra if systematic else ge.n_src + extra])
     gf.gf_encode_batched(items)
     torch.cuda.synchronize()
     coded = {i: (c, o.cpu().numpy()) for i, (c, o) in coded.items()}
@@ -592,8 +604,7 @@ def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30) -> dict:
         out = []
         for i, (ge, t) in enumerate(zip(batch.gens, times)):
             if i % 2 == 0:
-                out.append(serve.EncodeRequest(i, float(t), ge.field, ge.src,
-                                               np.ascontiguousarray(ge.coef_stream[:ge.n_src])))
+                out.append(serve.EncodeRequest(i, float(t), ge.field, ge.src, rows[i], systematic=systematic))
             else:
                 c, p = coded[i]
                 out.append(serve.DecodeRequest(i, float(t), ge.field, ge.n_src, ge.length, c, p,
@@ -610,10 +621,23 @@ def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30) -> dict:
     wall = srv.run(reqs)
     sat = n / wall
     good = ok(reqs)
+    # encode results: the same packets from one batched encode (a systematic request's first N
+    # packets are its sources)
+    enc = [r for r in reqs if isinstance(r, serve.EncodeRequest) and r.coef.shape[0]]
+    outs = [torch.empty((r.coef.shape[0], r.src.shape[1]), dtype=torch.uint8, device=dev) for r in enc]
+    srcs = [(torch.from_numpy(r.src).to(dev), torch.from_numpy(r.coef).to(dev)) for r in enc]
+    gf.gf_encode_batched([(r.field, r.src.shape[0], r.coef.shape[0], r.src.shape[1], s_, c_, o)
+                          for r, (s_, c_), o in zip(enc, srcs, outs)])
+    torch.cuda.synchronize()
+    for r, o in zip(enc, outs):
+        want = o.cpu().numpy()
+        good = good and np.array_equal(r.result[r.src.shape[0]:] if systematic else r.result, want)
+        if systematic:
+            good = good and np.array_equal(r.result[:r.src.shape[0]], r.src)
     launches = srv.launches
     rates = {}
     for f in fractions:
-        rate = f * sat
+        rate = f * (rate_base or sat)
         r2 = requests(synth.arrivals(rate, n, index=int(f * 100)), 20e-6)
         s2 = serve.Server(mem_budget=budget)
         w2 = s2.run(r2)
@@ -624,9 +648,11 @@ def serve_leg(torch, dev, n: int, fractions, budget: int = 4 << 30) -> dict:
         launches += s2.launches
     return {"requests": n, "saturation_req_per_s": sat, "saturation_wall_s": wall,
             "source_bytes": int(sum(ge.src.size for ge in batch.gens)), "rates": rates, "round_trip_ok": good,
-            "gpu_launches": launches, "device_memory_budget": budget,
-            "workload": f"{n} requests, half encode (K = N) and half decode, uneven shapes (N ~ U{{8..255}}, len "
-                        "log-uniform 64-9000 B, four fields), decode packets 20 us apart"}
+            "gpu_launches": launches, "device_memory_budget": budget, "systematic": systematic, "loss": loss,
+            "redundancy": redundancy,
+            "workload": f"{n} requests, half encode and half decode, uneven shapes (N ~ U{{8..255}}, len "
+                        f"log-uniform 64-9000 B, four fields), {'systematic' if systematic else 'random linear'} "
+                        f"coding, {int(loss * 100)}% losses, decode packets 20 us apart"}
 
 
 def run_serve(args, rank, world, local_rank):
@@ -650,6 +676,19 @@ def run_serve(args, rank, world, local_rank):
     plain_reqs = [serve.EncodeRequest(i, 0.0, ge.field, ge.src, np.ascontiguousarray(ge.coef_stream[:ge.n_src]))
                   for i, ge in enumerate(batch.gens)]
     plain_wall = serve.Server(max_active=1).run(plain_reqs)
+    # systematic against random linear coding, 0 % and 10 % losses, at one arrival rate per loss
+    # (half the random-linear saturation); encode requests add 15 % coded packets either way
+    compare = {}
+    for loss in (0.0, 0.1):
+        base = None
+        for sysm in (False, True):
+            leg2 = serve_leg(torch, dev, n, (0.5,), systematic=sysm, loss=loss, redundancy=0.15, rate_base=base)
+            base = base or leg2["saturation_req_per_s"]
+            key = f"{'systematic' if sysm else 'random'}_loss{int(loss * 100)}"
+            compare[key] = {"saturation_req_per_s": leg2["saturation_req_per_s"], "at_rate": leg2["rates"]["0.50x"],
+                            "round_trip_ok": leg2["round_trip_ok"]}
+            leg["gpu_launches"] += leg2["gpu_launches"]
+            leg["round_trip_ok"] = leg["round_trip_ok"] and leg2["round_trip_ok"]
     line = {"metric": "serving throughput req/s and p99 ms", "value": sat, "unit": "req/s", "n_gpus": world,
             "steps": 1, "warmup": 1, "ms_per_step": leg["saturation_wall_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
@@ -657,6 +696,7 @@ def run_serve(args, rank, world, local_rank):
                        "device_memory_budget": leg["device_memory_budget"], "source_bytes": leg["source_bytes"]},
             "saturation_GBps_source": leg["source_bytes"] / leg["saturation_wall_s"] / 1e9, "rates": leg["rates"],
             "plain_encode_req_per_s": len(plain_reqs) / plain_wall, "round_trip_ok": leg["round_trip_ok"],
+            "systematic_vs_random": compare,
             "clocks": clk.summary(), "gpu_launches": leg["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -153,11 +153,19 @@ int gf_encode_validate(const gf_gen_t *gens, int n_gens, gf_stream_t stream);
  *   used     device int32 or NULL: received rows consumed
  *   solved   device, n_src bytes or NULL: 1 where out row p is decoded
  */
+/* gf_dec_t.flags: the received packets are mostly sources sent uncoded
+ * (systematic coding: unit coding vectors).  The rows of the transform that
+ * such packets solve are unit vectors, so the payload phase runs on the
+ * table path, which skips zero multipliers: about (unit rows + missing
+ * sources x R) x len work instead of N x R x len.  Results are identical
+ * with or without the flag. */
+#define GF_DEC_SYSTEMATIC 1
+
 typedef struct gf_dec {
     int32_t field;
     int32_t n_src;    /* N, 0 <= N <= 1024 */
     int32_t n_recv;   /* R, 0 <= R <= 4096 */
-    int32_t reserved; /* must be 0 */
+    int32_t flags;    /* 0 or GF_DEC_SYSTEMATIC; other bits must be 0 */
     uint64_t len;
     const uint8_t *coef;
     const uint8_t *payload;
@@ -279,8 +287,11 @@ int gf_dec_open(int field, int n_src, int max_recv, uint64_t len, gf_decoder_t *
  * payload (n x len bytes), in host or device memory, copied into the
  * decoder's buffers with one cudaMemcpyAsync each on `stream` (host memory
  * must stay valid until the stream has run the copy; pinned memory keeps it
- * asynchronous).  Errors: GF_EINVAL (NULL pointers with n > 0, n < 0, or
- * more than max_recv packets in total), GF_ECUDA. */
+ * asynchronous).  Coding vectors in host memory are also read on the host
+ * for unit vectors (sources a systematic sender sent uncoded): a decoder
+ * whose packets are at least half unit vectors is decoded with
+ * GF_DEC_SYSTEMATIC by gf_dec_poll.  Errors: GF_EINVAL (NULL pointers with
+ * n > 0, n < 0, or more than max_recv packets in total), GF_ECUDA. */
 int gf_dec_push(gf_decoder_t *dec, const uint8_t *coef, const uint8_t *payload, int n, gf_stream_t stream);
 
 /* Enqueues on `stream` ONE batched decode over every decoder in decs[0..n)

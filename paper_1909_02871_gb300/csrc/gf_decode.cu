@@ -370,7 +370,7 @@ int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
     for (int i = 0; i < n_gens; ++i) {
         const gf_dec_t &d = gens[i];
         if (!field_ok(d.field) || d.n_src < 0 || d.n_src > kMaxDecodeN || d.n_recv < 0 ||
-            d.n_recv > kMaxDecodeR || d.reserved != 0)
+            d.n_recv > kMaxDecodeR || (d.flags & ~GF_DEC_SYSTEMATIC) != 0)
             return GF_EINVAL;
         if (!d.rank) return GF_EINVAL;
         if (d.n_src > 0 && d.len > 0 && !d.out) return GF_EINVAL;
@@ -405,6 +405,8 @@ int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
         e.n_src = d.n_recv;
         e.n_coded = d.n_src;
         e.coef_ld = d.n_recv;
+        // mostly unit rows in the transform: the table path skips their zero multipliers
+        e.path_hint = (d.flags & GF_DEC_SYSTEMATIC) ? GF_PATH_TABLE : 0;
     }
     w.x_bytes = x_bytes;
     w.grow_bytes = grow_bytes;

@@ -106,6 +106,7 @@ struct gf_decoder {
     int32_t *rank_host = nullptr;  // mapped pinned word written by the decode
     int32_t *rank_dev = nullptr;   // its device address
     int received = 0, tried = 0, last_rank = -1;
+    int unit_rows = 0;  // pushed coding vectors that are unit vectors (sources sent uncoded)
     std::shared_ptr<PollEvent> pending;  // the latest attempt, until its result is read
     DevicePool pool;
     // the last use of the buffers on every stream that touched them (push,
@@ -114,6 +115,31 @@ struct gf_decoder {
 };
 
 namespace {
+
+// Unit coding vectors among n rows of n_src coefficients in host memory (a
+// systematic sender's uncoded sources); 0 for rows in device memory, which
+// the host does not read.
+int count_unit_rows(const uint8_t *coef, int n, int n_src)
+{
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, coef) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (attr.type != cudaMemoryTypeHost && attr.type != cudaMemoryTypeUnregistered) return 0;
+    int units = 0;
+    for (int r = 0; r < n; ++r) {
+        const uint8_t *row = coef + (size_t)r * n_src;
+        int nz = 0, one = 0;
+        for (int i = 0; i < n_src && nz < 2; ++i)
+            if (row[i]) {
+                ++nz;
+                one = row[i] == 1;
+            }
+        units += (nz == 1 && one) ? 1 : 0;
+    }
+    return units;
+}
 
 int note_use(gf_decoder *d, cudaStream_t s)
 {
@@ -177,6 +203,7 @@ extern "C" int gf_dec_push(gf_decoder_t *d, const uint8_t *coef, const uint8_t *
     if (n == 0) return GF_OK;
     if (!coef || (d->len > 0 && !payload) || n > d->max_recv - d->received) return GF_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    d->unit_rows += count_unit_rows(coef, n, d->n_src);
     if (cudaMemcpyAsync(d->coef + (size_t)d->received * d->n_src, coef, (size_t)n * d->n_src, cudaMemcpyDefault,
                         s) != cudaSuccess)
         return GF_ECUDA;
@@ -207,6 +234,9 @@ extern "C" int gf_dec_poll(gf_decoder_t *const *decs, int n, gf_stream_t stream,
         g.payload = d->payload;
         g.out = d->out;
         g.rank = d->rank_dev;
+        // at least half of the packets are sources sent uncoded: the payload phase skips the
+        // zero multipliers of their unit transform rows
+        if (2 * d->unit_rows >= d->received) g.flags = GF_DEC_SYSTEMATIC;
         gens.push_back(g);
         tried.push_back(d);
     }

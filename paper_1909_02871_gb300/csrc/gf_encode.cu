@@ -128,6 +128,19 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
         for (int i = 0; i < WPT; ++i) acc[k][i] = 0u;
 
     for (int i = 0; i < N; ++i) {
+        // the tile's coefficients of source i first (the same for every lane): a source
+        // they all leave out is not loaded at all (sparse coding matrices, e.g. the transform
+        // of a decode whose received packets are mostly sources sent uncoded)
+        uint32_t c4[KPT / 4];  // four coefficients per register
+#pragma unroll
+        for (int q = 0; q < KPT / 4; ++q) c4[q] = 0u;
+#pragma unroll
+        for (int k = 0; k < KPT; ++k)
+            if (k < kn) c4[k >> 2] |= (uint32_t)__ldg(coefk + (size_t)k * ld + i) << (8 * (k & 3));
+        uint32_t any = 0u;
+#pragma unroll
+        for (int q = 0; q < KPT / 4; ++q) any |= c4[q];
+        if (any == 0u) continue;
         uint32_t w[WPT];
         load_words<WPT>(g.src + (size_t)i * len, col, len, w);
         Sel s[WPT];
@@ -135,13 +148,11 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
         for (int j = 0; j < WPT; ++j) s[j] = make_sel(w[j]);
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
-            if (k < kn) {
-                const uint32_t c = __ldg(coefk + (size_t)k * ld + i);
-                if (c != 0u) {
-                    const ByteMap m = ftab[c].m;
+            const uint32_t ck = (c4[k >> 2] >> (8 * (k & 3))) & 0xFFu;
+            if (ck != 0u) {
+                const ByteMap m = ftab[ck].m;
 #pragma unroll
-                    for (int j = 0; j < WPT; ++j) acc[k][j] ^= apply(m, s[j]);
-                }
+                for (int j = 0; j < WPT; ++j) acc[k][j] ^= apply(m, s[j]);
             }
         }
     }
@@ -349,7 +360,7 @@ int plan_batches(const std::vector<EncGen> &gens, int path, std::vector<EncodeBa
     const bool small_batch = gens.size() < (size_t)(2 * sm_count());
     for (const EncGen &g0 : gens) {
         EncGen g = g0;
-        int p = path;
+        int p = g0.path_hint ? g0.path_hint : path;
         if (p == GF_PATH_AUTO)
             p = small_batch && bitsliced_available() && bitsliced_supports(g)
                     ? GF_PATH_BITSLICED

@@ -22,7 +22,7 @@ struct EncGen {
     int variant;      // tile shape (table path) or 0 (bit-sliced path)
     int col_chunks;   // column tiles
     int k_chunks;     // coded-packet tiles
-    int pad;
+    int path_hint;    // 0, or the GF_PATH_* this generation takes whatever the batch's path
 };
 
 // Table-path tile shapes: (words per lane, coded packets per warp tile).

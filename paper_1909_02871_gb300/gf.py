@@ -17,6 +17,7 @@ from . import build as _build
 
 GF_OK, GF_EINVAL, GF_EOVERLAP, GF_ENOMEM, GF_ERANK, GF_ETIMEOUT, GF_ECUDA, GF_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
 GF_EBUSY = -8
+DEC_SYSTEMATIC = 1
 PATH_AUTO, PATH_TABLE, PATH_BITSLICED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -44,7 +45,7 @@ class GfRecode(ctypes.Structure):
 
 class GfDec(ctypes.Structure):
     _fields_ = [("field", ctypes.c_int32), ("n_src", ctypes.c_int32), ("n_recv", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("len", ctypes.c_uint64), ("coef", ctypes.c_void_p),
+                ("flags", ctypes.c_int32), ("len", ctypes.c_uint64), ("coef", ctypes.c_void_p),
                 ("payload", ctypes.c_void_p), ("out", ctypes.c_void_p), ("rank", ctypes.c_void_p),
                 ("used", ctypes.c_void_p), ("solved", ctypes.c_void_p)]
 
@@ -182,11 +183,13 @@ def make_gens(items) -> ctypes.Array:
 
 
 def make_decs(items) -> ctypes.Array:
-    """items: iterable of (field, n_src, n_recv, len, coef, payload, out, rank, used, solved)."""
+    """items: iterable of (field, n_src, n_recv, len, coef, payload, out, rank, used, solved[, flags])."""
     items = list(items)
     arr = (GfDec * max(1, len(items)))()
-    for i, (field, n_src, n_recv, length, coef, payload, out, rank, used, solved) in enumerate(items):
-        arr[i] = GfDec(field, n_src, n_recv, 0, length, _ptr(coef), _ptr(payload), _ptr(out), _ptr(rank),
+    for i, it in enumerate(items):
+        field, n_src, n_recv, length, coef, payload, out, rank, used, solved = it[:10]
+        flags = it[10] if len(it) > 10 else 0
+        arr[i] = GfDec(field, n_src, n_recv, flags, length, _ptr(coef), _ptr(payload), _ptr(out), _ptr(rank),
                        _ptr(used), _ptr(solved))
     return arr, len(items)
 

@@ -3,10 +3,15 @@
 Requests arrive over time (Poisson arrivals in the benchmark):
 
 * an encode request carries a generation (N source packets of len bytes) and
-  K coding vectors and wants the K coded packets (Eq. 2);
+  K coding vectors and wants the K coded packets (Eq. 2); a systematic one
+  sends the N sources first, uncoded (unit coding vectors: no arithmetic and
+  no device work), followed by its K coded packets;
 * a decode request names a generation (field, N, len) whose coded packets
   then arrive one by one; it completes when the packets received so far
-  determine all N sources (rank N) and returns them.
+  determine all N sources (rank N) and returns them.  Packets of a
+  systematic sender (unit coding vectors) are recognised by the library as
+  they are pushed, and a generation received mostly uncoded is decoded with
+  the payload phase that skips zero multipliers.
 
 The loop admits waiting requests while device memory (a fixed budget) and
 request slots allow, appends newly arrived packets of admitted decode requests
@@ -43,6 +48,7 @@ class EncodeRequest:
     result: np.ndarray | None = None
     done_at: float | None = None
     dev: dict = dc_field(default_factory=dict)
+    systematic: bool = False  # result = the N sources, then the K coded packets
 
     def device_bytes(self) -> int:
         K, N = self.coef.shape
@@ -208,7 +214,8 @@ class Server:
                 for r, h in zip(encs, copies[:len(encs)]):
                     K = r.coef.shape[0]
                     L = r.src.shape[1]
-                    r.result = h.numpy()[:K * L].reshape(K, L).copy()
+                    coded = h.numpy()[:K * L].reshape(K, L)
+                    r.result = np.concatenate([r.src, coded]) if r.systematic else coded.copy()
                     self._finish(r, t)
                     remaining -= 1
                 for r, h in zip(decs, copies[len(encs):]):

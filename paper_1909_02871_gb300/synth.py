@@ -155,6 +155,19 @@ def uneven_batch(n_gens: int = 2048, n_min: int = 8, n_max: int = 255, len_min: 
     return out
 
 
+def erasures(n: int, loss: float, *key: int) -> np.ndarray:
+    """n i.i.d. packet losses with probability ``loss`` (True = lost)."""
+    g = rng(W_MISC, 77, n, int(loss * 1000), *key)
+    return g.random(n) < loss
+
+
+def systematic_stream(coef_stream: np.ndarray) -> np.ndarray:
+    """A systematic sender's coding vectors: the N unit vectors (the sources
+    sent uncoded, in order) followed by the coded packets' vectors."""
+    n = coef_stream.shape[1]
+    return np.concatenate([np.eye(n, dtype=np.uint8), coef_stream])
+
+
 def arrivals(rate_per_s: float, n: int, index: int = 0) -> np.ndarray:
     """Poisson arrival times (seconds from 0) of n requests."""
     g = rng(W_SERVE, int(rate_per_s * 1000), n, index)

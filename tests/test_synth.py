@@ -78,3 +78,18 @@ def test_arrivals_are_poisson():
     # exponential gaps: mean 1/rate, coefficient of variation 1
     assert abs(gaps.mean() * rate - 1.0) < 5 / math.sqrt(n)
     assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05
+
+
+def test_systematic_stream_and_erasures():
+    """A systematic sender's stream: the N unit vectors in source order, then
+    the coded vectors unchanged; erasures are seeded and near their rate."""
+    g = synth.uneven_batch(n_gens=1, n_min=12, n_max=12, index=5).gens[0]
+    s = synth.systematic_stream(g.coef_stream)
+    assert s.shape == (12 + g.coef_stream.shape[0], 12) and s.dtype == np.uint8
+    assert np.array_equal(s[:12], np.eye(12, dtype=np.uint8))
+    assert np.array_equal(s[12:], g.coef_stream)
+    a = synth.erasures(20000, 0.1, 3)
+    assert np.array_equal(a, synth.erasures(20000, 0.1, 3))
+    assert not np.array_equal(a, synth.erasures(20000, 0.1, 4))
+    assert abs(a.mean() - 0.1) < 0.01
+    assert not synth.erasures(100, 0.0, 1).any()
