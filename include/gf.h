@@ -369,6 +369,14 @@ int gf_plan_destroy(gf_plan_t *plan);
 int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t len, int n_gens, gf_stream_t stream,
                        int *path, int *variant);
 
+/* gf_autotune_last: the candidates timed by this thread's last
+ * gf_autotune_encode call, in the order timed, with the mean device time of
+ * one batched encode (ms, three timed runs after a warm-up run) under each:
+ * up to `cap` entries into paths / variants / ms (any may be NULL); *n is
+ * set to the number of candidates.  The tuner's recorded choice is the
+ * candidate with the least time.  Errors: GF_EINVAL (cap < 0, n NULL). */
+int gf_autotune_last(int cap, int *paths, int *variants, float *ms, int *n);
+
 /* Record a choice for a bucket without timing (path GF_PATH_TABLE or
  * GF_PATH_BITSLICED, variant 0..3 = table tile shape). */
 int gf_autotune_set(int field, int n_src, int n_coded, uint64_t len, int path, int variant);

@@ -41,6 +41,8 @@ using TuneKey = std::tuple<int, int, int, int>;
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneChoice> g_tune;
 static thread_local int t_force_variant = -1;
+// the candidates and mean times of this thread's last gf_autotune_encode call
+static thread_local std::vector<std::pair<TuneChoice, float>> t_last_tune;
 
 static int log2_bucket(unsigned long long v)
 {
@@ -290,6 +292,7 @@ extern "C" int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t le
     float best = 1e30f;
     TuneChoice pick{GF_PATH_TABLE, choose_table_variant(field, n_src, n_coded, len)};
     int st = GF_OK;
+    t_last_tune.clear();
     for (const TuneChoice &c : cands) {
         t_force_variant = c.path == GF_PATH_TABLE ? c.variant : -1;
         float total = 0.f;
@@ -309,6 +312,7 @@ extern "C" int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t le
             st = ok;
             break;
         }
+        t_last_tune.emplace_back(c, total / 3.f);
         if (total < best) {
             best = total;
             pick = c;
@@ -325,6 +329,18 @@ extern "C" int gf_autotune_encode(int field, int n_src, int n_coded, uint64_t le
     }
     if (out_path) *out_path = pick.path;
     if (out_variant) *out_variant = pick.variant;
+    return GF_OK;
+}
+
+extern "C" int gf_autotune_last(int cap, int *paths, int *variants, float *ms, int *n)
+{
+    if (cap < 0 || !n) return GF_EINVAL;
+    *n = (int)t_last_tune.size();
+    for (int i = 0; i < *n && i < cap; ++i) {
+        if (paths) paths[i] = t_last_tune[i].first.path;
+        if (variants) variants[i] = t_last_tune[i].first.variant;
+        if (ms) ms[i] = t_last_tune[i].second;
+    }
     return GF_OK;
 }
 

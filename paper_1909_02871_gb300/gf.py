@@ -75,6 +75,8 @@ _SIGS = {
     "gf_autotune_encode": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
+    "gf_autotune_last": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int)]),
     "gf_autotune_set": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                        ctypes.c_int]),
     "gf_autotune_query": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
@@ -352,6 +354,17 @@ def gf_autotune_encode(field: int, n_src: int, n_coded: int, length: int, n_gens
     _check(load().gf_autotune_encode(field, n_src, n_coded, length, n_gens, _stream(stream), ctypes.byref(p),
                                      ctypes.byref(v)), "gf_autotune_encode")
     return p.value, v.value
+
+
+def gf_autotune_last():
+    """[(path, variant, mean ms)] of the candidates this thread's last
+    gf_autotune_encode call timed."""
+    n = ctypes.c_int()
+    _check(load().gf_autotune_last(0, None, None, None, ctypes.byref(n)), "gf_autotune_last")
+    k = n.value
+    paths, variants, ms = (ctypes.c_int * max(k, 1))(), (ctypes.c_int * max(k, 1))(), (ctypes.c_float * max(k, 1))()
+    _check(load().gf_autotune_last(k, paths, variants, ms, ctypes.byref(n)), "gf_autotune_last")
+    return [(paths[i], variants[i], float(ms[i])) for i in range(k)]
 
 
 def gf_autotune_set(field: int, n_src: int, n_coded: int, length: int, path: int, variant: int) -> None:
