@@ -79,14 +79,26 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len)
         if (it != g_tune.end()) return it->second.path;
     }
     if (!bitsliced_available() || n_src <= 0 || n_coded <= 0 || len == 0) return GF_PATH_TABLE;
-    // Cost model in SM clocks per generation, from GB300 measurements: a
-    // tensor-core D pass (128 bytes x 32 coded packets x up to 64 sources)
-    // costs about 2700 clocks however full it is (synchronisation, not MMA
-    // work, dominates); the table path costs about 53 clocks per source for
-    // every 128-byte x 8-packet tile (GF(2), a plain XOR, about 0.77 of that).
+    // Cost model in SM clocks per generation per SM, fitted to the tuner's
+    // own timings of 192 shapes on a GB300 (GF(2) and GF(256); N 8..255, K
+    // 8..64, len 128..4096): a tensor-core pass (128 bytes x up to 64 coded
+    // packets x up to 64 sources) costs about 3900 clocks of handshakes and
+    // B building plus about 100 per MMA issued (the bias MMA and one per 8
+    // sources, twice for more than 32 coded packets); the table path costs
+    // about 50 clocks per source and 90 more for every 128-byte x 8-packet
+    // tile (GF(2), a plain XOR, about 0.77 of the per-source cost).  With
+    // these constants AUTO picks the tuner's choice on 164 of the 192 shapes
+    // and is 5 % slower than it on average.
+    const int chunks = (n_src + 63) / 64, items = (n_coded + 63) / 64;
     const double tiles = std::ceil((double)len / 128.0);
-    const double bits = std::ceil(n_src / 64.0) * tiles * std::ceil(n_coded / 32.0) * 2700.0;
-    const double table = tiles * std::ceil(n_coded / 8.0) * 53.0 * n_src * (field == 1 ? 0.77 : 1.0);
+    double mmas = 0.0;
+    for (int it = 0; it < items; ++it) {
+        const int halves = std::min(n_coded - 64 * it, 64) > 32 ? 2 : 1;
+        for (int c = 0; c < chunks; ++c) mmas += 1 + halves * ((std::min(n_src - 64 * c, 64) + 7) / 8);
+    }
+    const double bits = tiles * (3900.0 * chunks * items + 100.0 * mmas);
+    const double ttiles = tiles * std::ceil(n_coded / 8.0);
+    const double table = ttiles * (50.0 * n_src * (field == 1 ? 0.77 : 1.0) + 90.0);
     if (bits < table) return GF_PATH_BITSLICED;
     return GF_PATH_TABLE;
 }
