@@ -127,6 +127,10 @@ struct Ctl {
     int abort;
 };
 
+static_assert(sizeof(Ctl) <= 1024, "control block (below the B halves)");
+static_assert((kBiasBBytes + kTabBytes + kStageAll + 1024) % 1024 == 0, "B halves 1024-aligned");
+static_assert(2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 + 1023 <= kSmemBytes, "shared memory");
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned long long now_ns()
@@ -413,11 +417,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *Bs = smem;                                // two B buffers
-    unsigned char *bias_b = smem + 2 * kBBytes;
+    // the bias operand, tables, staging and control first, the two B halves above them (with a B
+    // half at the bottom of shared memory its MMAs ran about a third slower, measured)
+    unsigned char *bias_b = smem;
     uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][field][c]
     unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
     Ctl *ctl = reinterpret_cast<Ctl *>(staging + kStageAll);
+    unsigned char *Bs = staging + kStageAll + 1024;                  // two B buffers (1024-aligned)
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
