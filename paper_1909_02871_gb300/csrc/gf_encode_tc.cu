@@ -107,12 +107,11 @@ constexpr long long kSentinel = -1;
 constexpr int kKBlock = kDN * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
 constexpr int kBBytes = 2 * kKBlock;        // 64 KB: one B half (K <= 512, 32 coded packets)
 constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
-// 8x8 E2M1 blocks of every coefficient of GF(256), GF(16), GF(4), GF(2):
-// row r of the block of c in field GF(2^n) is word 8 * (base(n) + c) + r
-// (one 32-byte block per coefficient, read with two 16-byte loads)
-constexpr int kTabBase8 = 0, kTabBase4 = 8 * 256, kTabBase2 = 8 * 256 + 16, kTabBase1 = 8 * 256 + 16 + 4;
-constexpr int kTabRow = 256;
-constexpr int kTabBytes = 16 * 1024;
+// The unit images of every coefficient of GF(256), GF(16), GF(4), GF(2): 8
+// bytes per coefficient (entry base(n) + c), from which block_row builds
+// the rows of its 8x8 block
+constexpr int kTabBase8 = 0, kTabBase4 = 256, kTabBase2 = 256 + 16, kTabBase1 = 256 + 16 + 4;
+constexpr int kTabBytes = 16 * 1024;  // 2.2 KB used; the region keeps the B halves where they were measured
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
 constexpr int kSmemBytes = 2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*slack*/;
 
@@ -295,16 +294,29 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
 constexpr uint32_t kIdesc = (0u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kDN >> 3) << 17) | (1u << 23) |
                             ((uint32_t)(128 >> 4) << 24);
 
-// the 8 E2M1 values (nibbles j = 0..7) of one source byte: 1.0 (0x2) where
-// bit j is set.  Bit j moves to bit 4j + 1 in three halving steps (nibbles
-// apart, then bit pairs, then bits), without a table lookup: shared-memory
-// lookups here contended with the tensor core's operand reads.
+// The 8 bits of a source byte take the K order (0, 4, 1, 5, 2, 6, 3, 7):
+// nibble 2i holds bit i and nibble 2i + 1 bit i + 4 (any order serves, as
+// long as the coefficient blocks use the same one; this one makes both
+// sides cheap to build).
+//
+// The 8 E2M1 values of one source byte, 1.0 (0x2) where its bit is set, in
+// that order: two halving steps move bits 0..3 to bits 8i and bits 4..7 to
+// bits 8i + 4, without a table lookup (shared-memory lookups here contended
+// with the tensor core's operand reads).
 __device__ __forceinline__ uint32_t spread_bits(uint32_t b)
 {
-    uint32_t x = (b | (b << 12)) & 0x000F000Fu;
-    x = (x | (x << 6)) & 0x03030303u;
-    x = (x | (x << 3)) & 0x11111111u;
+    uint32_t x = (b | (b << 14)) & 0x00330033u;
+    x = (x | (x << 7)) & 0x11111111u;
     return x << 1;
+}
+
+// Row r of a coefficient's 8x8 block in the same K order: nibble 2i is bit r
+// of p_i and nibble 2i + 1 bit r of p_(i+4), where p_j (byte j of the pair
+// P: bytes 0..3 in .x, 4..7 in .y) is the image of the unit byte with bit j
+// set under the coefficient's map.
+__device__ __forceinline__ uint32_t block_row(uint2 P, int r)
+{
+    return ((((P.x >> r) & 0x01010101u) | (((P.y >> r) & 0x01010101u) << 4)) << 1);
 }
 
 // parity byte of 8 biased sums, low 16 bits packed two per word (word j =
@@ -420,7 +432,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     // the bias operand, tables, staging and control first, the two B halves above them (with a B
     // half at the bottom of shared memory its MMAs ran about a third slower, measured)
     unsigned char *bias_b = smem;
-    uint32_t *tab = reinterpret_cast<uint32_t *>(bias_b + kBiasBBytes);  // [r][field][c]
+    uint2 *tab = reinterpret_cast<uint2 *>(bias_b + kBiasBBytes);  // [field][c]: unit images
     unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
     Ctl *ctl = reinterpret_cast<Ctl *>(staging + kStageAll);
     unsigned char *Bs = staging + kStageAll + 1024;                  // two B buffers (1024-aligned)
@@ -429,34 +441,17 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // The 8x8 E2M1 block of every coefficient of every field.  A byte holds
-    // 8/n words of GF(2^n) (word w in bits [wn, wn+n)), all multiplied by
-    // the same c, so the block is block-diagonal: output bit r (word r/n,
-    // bit r%n), input bit j (word j/n, bit j%n) is bit r%n of c*x^(j%n)
-    // when both lie in the same word.  Row r is one word, nibble j = that
-    // bit; a coefficient's 8 rows are contiguous (one 32-byte block).
-    for (int e = tid; e < 8 * 256; e += blockDim.x) {
-        const uint32_t c = (uint32_t)e & 255u, r = (uint32_t)e >> 8;
-        uint32_t p = c, row = 0;
-        for (int j = 0; j < 8; ++j) {
-            if ((p >> r) & 1u) row |= kOne << (4 * j);
-            p = xtime(8, p);
-        }
-        tab[e] = row;
-    }
-    if (kAnyField) {
-        for (int e = tid; e < 8 * 22; e += blockDim.x) {
-            const int r = e / 22, col = e % 22;
-            const int lg = col < 16 ? 2 : col < 20 ? 1 : 0;  // n = 2^lg
-            const int n = 1 << lg;
-            const uint32_t c = (uint32_t)(lg == 2 ? col : lg == 1 ? col - 16 : col - 20);
-            uint32_t row = 0, p = c;
-            for (int j = 0; j < 8; ++j) {
-                p = (j & (n - 1)) == 0 ? c : xtime(n, p);  // c * x^(j % n)
-                if ((r >> lg) == (j >> lg) && ((p >> (r & (n - 1))) & 1u)) row |= kOne << (4 * j);
-            }
-            tab[kTabBase4 + r * kTabRow + col] = row;
-        }
+    // The unit images of every coefficient of every field.  A byte holds 8/n
+    // words of GF(2^n) (word w in bits [wn, wn+n)), all multiplied by the
+    // same c, so the image of the unit byte with bit j set is c * x^(j%n)
+    // placed in word j/n: the block of c is block-diagonal.
+    for (int e = tid; e < 256 + (kAnyField ? 22 : 0); e += blockDim.x) {
+        const int n = e < kTabBase4 ? 8 : e < kTabBase2 ? 4 : e < kTabBase1 ? 2 : 1;
+        const uint32_t c = (uint32_t)(e - (n == 8 ? kTabBase8 : n == 4 ? kTabBase4 : n == 2 ? kTabBase2 : kTabBase1));
+        uint2 P;
+        P.x = unit_image(n, c, 0) | (unit_image(n, c, 1) << 8) | (unit_image(n, c, 2) << 16) | (unit_image(n, c, 3) << 24);
+        P.y = unit_image(n, c, 4) | (unit_image(n, c, 5) << 8) | (unit_image(n, c, 6) << 16) | (unit_image(n, c, 7) << 24);
+        tab[e] = P;
     }
     // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
     for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x) {
@@ -555,7 +550,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const uint8_t *coef = g.coef;
             const int nkc = (N + kMaxSrc - 1) / kMaxSrc;  // chunks of 64 sources
             const int field = g.field;
-            const uint32_t *ftab =
+            const uint2 *ftab =
                 kAnyField ? tab + (field == 8 ? kTabBase8 : field == 4 ? kTabBase4 : field == 2 ? kTabBase2 : kTabBase1)
                           : tab;
             const int nh = (min(kCodedPerItem, K - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
@@ -587,14 +582,14 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     for (int t = 0; t < 4; ++t) {
                         const int kp = kq * 4 + t;  // packet of the half = column slot
                         const uint32_t w = cc[t];
+                        // unit images of the 4 coefficients (sources 4m .. 4m + 3), then the 8 rows
+                        uint2 P[4];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) P[x] = ftab[(w >> (8 * x)) & 0xFFu];
 #pragma unroll
                         for (int r = 0; r < 8; ++r) {
-                            const uint32_t *tr = ftab + r * kTabRow;
-                            uint4 q;
-                            q.x = tr[w & 0xFFu];
-                            q.y = tr[(w >> 8) & 0xFFu];
-                            q.z = tr[(w >> 16) & 0xFFu];
-                            q.w = tr[w >> 24];
+                            const uint4 q = make_uint4(block_row(P[0], r), block_row(P[1], r), block_row(P[2], r),
+                                                       block_row(P[3], r));
                             *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, kb, m)) = q;
                         }
                     }

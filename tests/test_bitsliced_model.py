@@ -159,3 +159,39 @@ def test_encode_with_two_packets_per_column(n):
             out_bits[kp] ^= (word[8 * slot:8 * slot + 8] >> (10 * half)) & 1
     out = (out_bits[:K] << np.arange(8)[None, :, None]).sum(axis=1).astype(np.uint8)
     assert np.array_equal(out, oracle.encode(n, src, coef))
+
+
+def test_permuted_bit_order_of_the_kernel():
+    """The kernel orders the 8 bits of a source byte as (0, 4, 1, 5, 2, 6, 3, 7)
+    along K, on both sides: the source side spreads a byte with two halving
+    steps, the coefficient side builds row r of a block from the unit images
+    p_j (the image of the unit byte with bit j set) with a shift and two
+    masks.  Restated here bit for bit, the nibble-wise dot product of row r
+    with the spread byte a has the parity of bit r of c*a, for every
+    coefficient, byte and field."""
+    order = [0, 4, 1, 5, 2, 6, 3, 7]
+
+    def spread(b):
+        x = (b | (b << 14)) & 0x00330033
+        x = (x | (x << 7)) & 0x11111111
+        return (x << 1) & 0xFFFFFFFF
+
+    def block_row(px, py, r):
+        return (((px >> r) & 0x01010101) | (((py >> r) & 0x01010101) << 4)) << 1
+
+    for b in range(256):
+        w = spread(b)
+        for k in range(8):
+            assert ((w >> (4 * k)) & 0xF) == (2 if (b >> order[k]) & 1 else 0)
+    for n in FIELDS:
+        for c in range(1 << n):
+            imgs = [int(oracle.region_mul(n, np.array([1 << j], np.uint8), c)[0]) for j in range(8)]
+            px = imgs[0] | imgs[1] << 8 | imgs[2] << 16 | imgs[3] << 24
+            py = imgs[4] | imgs[5] << 8 | imgs[6] << 16 | imgs[7] << 24
+            rows = [block_row(px, py, r) for r in range(8)]
+            for a in range(256):
+                wa = spread(a)
+                prod = int(oracle.region_mul(n, np.array([a], np.uint8), c)[0])
+                for r in range(8):
+                    dot = sum(((rows[r] >> (4 * k)) & 0xF) * ((wa >> (4 * k)) & 0xF) for k in range(8)) // 4
+                    assert dot % 2 == (prod >> r) & 1, (n, c, a, r)
