@@ -7,9 +7,11 @@ GF(q)).  The sender encodes coded packets in the order of its coding-vector
 stream until the receiver holds N_g innovative packets; a packet is lost with
 the workload's erasure probability.  One step of the pipeline is:
 
-1. one persistent encode launch over every generation: the packets that
-   arrive are written contiguously into the receiver's buffer, the lost ones
-   into a discard buffer (the sender does the work for both);
+1. one persistent encode launch over every generation: the sender encodes
+   every packet it sends, written per generation as the packets that arrive
+   followed by the lost ones (the sender does the work for both; one
+   generation of K = received + lost packets keeps the launch's work items
+   full);
 2. one batched decode over every generation from its received packets.
 
 Both launches come from plans, so a step is captured once in a CUDA graph and
@@ -75,21 +77,19 @@ def build(batch: synth.UnevenBatch, device=None) -> UnevenWork:
         recv_rows.append(sent[~g.erased[:k]])
         lost_rows.append(sent[g.erased[:k]])
 
-    # device buffers, one contiguous allocation per kind
-    src_off, rc_off, lc_off, rv_off, ls_off, out_off = [], [], [], [], [], []
-    s = rc = lc = rv = ls = 0
+    # device buffers, one contiguous allocation per kind; per generation the sent packets (and
+    # their coding vectors) are the received ones followed by the lost ones
+    src_off, cs_off, st_off = [], [], []
+    s = cs = st = 0
     for g, rr, lr in zip(gens, recv_rows, lost_rows):
         src_off.append(s); s += g.src.size
-        rc_off.append(rc); rc += rr.size * g.n_src
-        lc_off.append(lc); lc += lr.size * g.n_src
-        rv_off.append(rv); rv += rr.size * g.length
-        ls_off.append(ls); ls += lr.size * g.length
+        cs_off.append(cs); cs += (rr.size + lr.size) * g.n_src
+        st_off.append(st); st += (rr.size + lr.size) * g.length
     d = {
         "src": _cat(torch, [g.src for g in gens], dev),
-        "coef_recv": _cat(torch, [g.coef_stream[r] for g, r in zip(gens, recv_rows)], dev),
-        "coef_lost": _cat(torch, [g.coef_stream[r] for g, r in zip(gens, lost_rows)], dev),
-        "recv": torch.zeros(max(rv, 1), dtype=torch.uint8, device=dev),
-        "lost": torch.zeros(max(ls, 1), dtype=torch.uint8, device=dev),
+        "coef_sent": _cat(torch, [g.coef_stream[np.concatenate([r, l])] for g, r, l in
+                                  zip(gens, recv_rows, lost_rows)], dev),
+        "sent": torch.zeros(max(st, 1), dtype=torch.uint8, device=dev),
         "out": torch.zeros(max(s, 1), dtype=torch.uint8, device=dev),
         "rank": torch.zeros(len(gens), dtype=torch.int32, device=dev),
         "used": torch.zeros(len(gens), dtype=torch.int32, device=dev),
@@ -97,14 +97,13 @@ def build(batch: synth.UnevenBatch, device=None) -> UnevenWork:
     base = {k: int(v.data_ptr()) for k, v in d.items()}
     enc, dec = [], []
     for i, (g, rr, lr) in enumerate(zip(gens, recv_rows, lost_rows)):
-        enc.append((g.field, g.n_src, rr.size, g.length, base["src"] + src_off[i], base["coef_recv"] + rc_off[i],
-                    base["recv"] + rv_off[i]))
-        enc.append((g.field, g.n_src, lr.size, g.length, base["src"] + src_off[i], base["coef_lost"] + lc_off[i],
-                    base["lost"] + ls_off[i]))
-        dec.append((g.field, g.n_src, rr.size, g.length, base["coef_recv"] + rc_off[i], base["recv"] + rv_off[i],
+        enc.append((g.field, g.n_src, rr.size + lr.size, g.length, base["src"] + src_off[i],
+                    base["coef_sent"] + cs_off[i], base["sent"] + st_off[i]))
+        dec.append((g.field, g.n_src, rr.size, g.length, base["coef_sent"] + cs_off[i], base["sent"] + st_off[i],
                     base["out"] + src_off[i], base["rank"] + 4 * i, base["used"] + 4 * i, None))
     d["_src_off"] = src_off
-    return UnevenWork(batch, k_sent, recv_rows, lost_rows, d, enc, dec, int(s), int(rv + ls))
+    d["_sent_off"] = st_off
+    return UnevenWork(batch, k_sent, recv_rows, lost_rows, d, enc, dec, int(s), int(st))
 
 
 class UnevenStep:
@@ -146,8 +145,24 @@ def plain_step(work: UnevenWork, gens=None, stream=None) -> None:
     """The plain form: one encode call and one decode call per generation."""
     idx = range(len(work.dec_items)) if gens is None else gens
     for i in idx:
-        gf.gf_encode_batched([work.enc_items[2 * i], work.enc_items[2 * i + 1]], stream=stream)
+        gf.gf_encode_batched([work.enc_items[i]], stream=stream)
         gf.gf_decode_batched([work.dec_items[i]], stream=stream)
+
+
+def received(work: UnevenWork, i: int) -> np.ndarray:
+    """The coded packets generation i's receiver got (host copy), in arrival order."""
+    g = work.batch.gens[i]
+    off = work.dev["_sent_off"][i]
+    n = work.recv_rows[i].size * g.length
+    return work.dev["sent"][off:off + n].cpu().numpy().reshape(-1, g.length)
+
+
+def lost(work: UnevenWork, i: int) -> np.ndarray:
+    """The coded packets generation i's sender sent that were lost (host copy)."""
+    g = work.batch.gens[i]
+    off = work.dev["_sent_off"][i] + work.recv_rows[i].size * g.length
+    n = work.lost_rows[i].size * g.length
+    return work.dev["sent"][off:off + n].cpu().numpy().reshape(-1, g.length)
 
 
 def decoded(work: UnevenWork, i: int) -> np.ndarray:
