@@ -391,10 +391,33 @@ int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
         g.W = (int)align_up((size_t)d.n_src + (size_t)d.n_recv, 16);
         g.x_off = x_bytes;
         x_bytes += align_up((size_t)g.N * g.R, 256);
-        const bool in_smem = dec_smem_bytes(g.field, g.N, g.W, true) <= limit;
-        g.grow_off = in_smem ? (size_t)-1 : grow_bytes;
-        if (!in_smem) grow_bytes += align_up((size_t)g.N * g.W, 256);
-        w.smem = std::max(w.smem, dec_smem_bytes(g.field, g.N, g.W, in_smem));
+        g.blk = -1;
+        g.grow_off = (size_t)-1;
+        if (g.R > 0 && blk_eligible(g.field, g.N, g.R, g.W)) {
+            // many sources: the blocked coefficient phase, its scratch in the rows region
+            BlkGen b{};
+            b.coef = d.coef;
+            b.rank_out = d.rank;
+            b.used_out = d.used;
+            b.solved = d.solved;
+            b.field = d.field;
+            b.N = g.N;
+            b.R = g.R;
+            b.W = g.W;
+            b.off = grow_bytes;
+            grow_bytes += align_up(blk_scratch_bytes(b), 256);
+            g.blk = (int)w.blk.size();
+            w.blk.push_back(b);
+            w.blk_max_w = std::max(w.blk_max_w, g.W);
+            w.blk_max_n = std::max(w.blk_max_n, g.N);
+        } else {
+            const bool in_smem = dec_smem_bytes(g.field, g.N, g.W, true) <= limit;
+            if (!in_smem) {
+                g.grow_off = grow_bytes;
+                grow_bytes += align_up((size_t)g.N * g.W, 256);
+            }
+            w.smem = std::max(w.smem, dec_smem_bytes(g.field, g.N, g.W, in_smem));
+        }
         EncGen &e = apply[i];
         e = EncGen{};
         e.src = d.payload;
@@ -414,7 +437,8 @@ int build_decode(const gf_dec_t *gens, int n_gens, DecodeWork &w)
     return GF_OK;
 }
 
-// Place X / global rows at `dev_x`, then build the apply batches.
+// Place X / global rows at `dev_x`, then build the apply batches and the
+// blocked generations' row-product batches.
 int place_decode(DecodeWork &w, char *dev_x, char *dev_rows)
 {
     for (size_t i = 0; i < w.gens.size(); ++i) {
@@ -422,16 +446,34 @@ int place_decode(DecodeWork &w, char *dev_x, char *dev_rows)
         g.X = reinterpret_cast<uint8_t *>(dev_x + g.x_off);
         g.grows = g.grow_off == (size_t)-1 ? nullptr : reinterpret_cast<uint8_t *>(dev_rows + g.grow_off);
         w.apply[i].coef = g.X;
+        if (g.blk >= 0) {
+            BlkGen &b = w.blk[g.blk];
+            b.X = g.X;
+            blk_place(b, dev_rows + b.off);
+        }
     }
-    return plan_batches(w.apply, GF_PATH_AUTO, w.batches);
+    int st = plan_batches(w.apply, GF_PATH_AUTO, w.batches);
+    if (st != GF_OK) return st;
+    int max_r = 0;
+    for (const BlkGen &b : w.blk) max_r = std::max(max_r, b.R);
+    const int steps = (max_r + kBlkRows - 1) / kBlkRows;
+    w.prod1.assign(steps, {});
+    w.prod2.assign(steps, {});
+    std::vector<EncGen> p1, p2;
+    for (int s = 0; s < steps; ++s) {
+        blk_products(w.blk, s, p1, p2);
+        if (!p1.empty() && (st = plan_batches(p1, GF_PATH_AUTO, w.prod1[s])) != GF_OK) return st;
+        if (!p2.empty() && (st = plan_batches(p2, GF_PATH_AUTO, w.prod2[s])) != GF_OK) return st;
+    }
+    return GF_OK;
 }
 
 int launch_decode_coef(const DecodeWork &w, const DecGen *d_gens, cudaStream_t stream)
 {
-    if (w.gens.empty()) return GF_OK;
+    if (w.n_coef == 0) return GF_OK;
     const int st = configure_decode_coef();
     if (st != GF_OK) return st;
-    decode_coef_kernel<<<(unsigned)w.gens.size(), kDecThreads, w.smem, stream>>>(d_gens);
+    decode_coef_kernel<<<(unsigned)w.n_coef, kDecThreads, w.smem, stream>>>(d_gens);
     return cuda_status(cudaGetLastError());
 }
 
@@ -450,28 +492,56 @@ size_t decode_stage_bytes(const DecodeWork &w)
 {
     size_t b = align_up(w.gens.size() * sizeof(DecGen), 256);
     for (const auto &bt : w.batches) b += batch_bytes(bt);
+    b += align_up(w.blk.size() * sizeof(BlkGen), 256);
+    for (const auto &step : w.prod1)
+        for (const auto &bt : step) b += batch_bytes(bt);
+    for (const auto &step : w.prod2)
+        for (const auto &bt : step) b += batch_bytes(bt);
     return b;
+}
+
+// Work counters a staged decode needs (one per batched launch).
+size_t decode_counters(const DecodeWork &w)
+{
+    size_t n = w.batches.size();
+    for (const auto &step : w.prod1) n += step.size();
+    for (const auto &step : w.prod2) n += step.size();
+    return n;
 }
 
 // Serialise DecGens + apply batches into host at `off`, device pointers
 // relative to dev_base; returns the new offset.
 size_t stage_decode(DecodeWork &w, char *host, char *dev_base, size_t off, WorkCounter *counters)
 {
-    const size_t gb = w.gens.size() * sizeof(DecGen);
-    // one CTA per generation, scheduled roughly in block order: the most
-    // expensive eliminations (N^2 (N + R) row operations) go first so that
-    // none of them starts near the end of the launch
-    std::vector<DecGen> order(w.gens);
+    // one CTA per generation of decode_coef_kernel, scheduled roughly in block order: the most
+    // expensive eliminations (N^2 (N + R) row operations) go first so that none of them starts
+    // near the end of the launch (blocked generations are not its work)
+    std::vector<DecGen> order;
+    for (const DecGen &g : w.gens)
+        if (g.blk < 0) order.push_back(g);
     std::stable_sort(order.begin(), order.end(), [](const DecGen &a, const DecGen &b) {
         return (double)a.N * a.N * (a.N + a.R) > (double)b.N * b.N * (b.N + b.R);
     });
-    memcpy(host + off, order.data(), gb);
+    w.n_coef = (int)order.size();
+    const size_t gb = order.size() * sizeof(DecGen);
+    if (gb) memcpy(host + off, order.data(), gb);
     w.d_gens = reinterpret_cast<DecGen *>(dev_base + off);
-    off += align_up(gb, 256);
+    off += align_up(w.gens.size() * sizeof(DecGen), 256);
+    size_t c = 0;
     for (size_t i = 0; i < w.batches.size(); ++i) {
-        w.batches[i].d_counter = counters + i;
+        w.batches[i].d_counter = counters + c++;
         off = stage_batch(w.batches[i], host, dev_base, off);
     }
+    const size_t bb = w.blk.size() * sizeof(BlkGen);
+    if (bb) memcpy(host + off, w.blk.data(), bb);
+    w.d_blk = reinterpret_cast<BlkGen *>(dev_base + off);
+    off += align_up(bb, 256);
+    for (auto *prods : {&w.prod1, &w.prod2})
+        for (auto &step : *prods)
+            for (auto &bt : step) {
+                bt.d_counter = counters + c++;
+                off = stage_batch(bt, host, dev_base, off);
+            }
     return off;
 }
 
@@ -479,6 +549,19 @@ int launch_decode(const DecodeWork &w, cudaStream_t stream)
 {
     int st = launch_decode_coef(w, w.d_gens, stream);
     if (st != GF_OK) return st;
+    if (!w.blk.empty()) {
+        const int nb = (int)w.blk.size();
+        if ((st = launch_blk_init(w.d_blk, nb, stream)) != GF_OK) return st;
+        for (size_t s = 0; s < w.prod1.size(); ++s) {
+            if ((st = launch_blk_prepare(w.d_blk, nb, (int)s, stream)) != GF_OK) return st;
+            for (const auto &b : w.prod1[s])
+                if ((st = launch_batch(b, stream)) != GF_OK) return st;
+            if ((st = launch_blk_gj(w.d_blk, nb, (int)s, w.blk_max_w, stream)) != GF_OK) return st;
+            for (const auto &b : w.prod2[s])
+                if ((st = launch_batch(b, stream)) != GF_OK) return st;
+        }
+        if ((st = launch_blk_final(w.d_blk, nb, w.blk_max_n, stream)) != GF_OK) return st;
+    }
     for (const auto &b : w.batches) {
         st = launch_batch(b, stream);
         if (st != GF_OK) return st;
@@ -502,6 +585,7 @@ static int decode_batched_impl(const gf_dec_t *gens, int n_gens, cudaStream_t st
     st = place_decode(w, (char *)ws->dev + kCounterBytes, (char *)ws->dev + kCounterBytes + x_total);
     if (st != GF_OK) return st;
     const size_t stage = decode_stage_bytes(w);
+    if (decode_counters(w) > kCounterBytes / sizeof(WorkCounter)) return GF_EINVAL;
     st = ws->reserve_device(kCounterBytes + x_total + r_total + stage, stream);
     if (st != GF_OK) return st;
     char *dev_x = (char *)ws->dev + kCounterBytes;

@@ -157,8 +157,18 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
         }
     }
 #pragma unroll
-    for (int k = 0; k < KPT; ++k)
-        if (k < kn) store_words<WPT>(g.out + (size_t)(k0 + k) * len, col, len, acc[k]);
+    for (int k = 0; k < KPT; ++k) {
+        if (k < kn) {
+            if (g.accumulate) {
+                // out ^= the products (the blocked decode's row updates)
+                uint32_t old[WPT];
+                load_words<WPT>(g.out + (size_t)(k0 + k) * len, col, len, old);
+#pragma unroll
+                for (int i = 0; i < WPT; ++i) acc[k][i] ^= old[i];
+            }
+            store_words<WPT>(g.out + (size_t)(k0 + k) * len, col, len, acc[k]);
+        }
+    }
 }
 
 __device__ __forceinline__ int find_gen(const long long *tile_start, int n_gens, long long t)

@@ -23,6 +23,7 @@ struct EncGen {
     int col_chunks;   // column tiles
     int k_chunks;     // coded-packet tiles
     int path_hint;    // 0, or the GF_PATH_* this generation takes whatever the batch's path
+    int accumulate;   // 1: out ^= the products (the blocked decode's GEMMs), 0: out = the products
 };
 
 // Table-path tile shapes: (words per lane, coded packets per warp tile).

@@ -725,8 +725,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int nlo = min(8, g.n_coded - klo), nhi = min(8, g.n_coded - khi);  // live packets
             bool ok = true;
             for (int v = 0; v < nunits; ++v) {
-                const bool first = v < ncols;  // source chunk 0 writes, later chunks add (XOR) their share
-                const int ct = first ? v : v % ncols;
+                // source chunk 0 writes (or, accumulating, adds into the output), later chunks add (XOR)
+                const bool first = v < ncols && !g.accumulate;
+                const int ct = v % ncols;
                 if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;

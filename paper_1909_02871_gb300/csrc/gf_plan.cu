@@ -212,6 +212,10 @@ extern "C" int gf_decode_plan_create(const gf_dec_t *gens, int n_gens, gf_plan_t
         return st;
     }
     const size_t stage = decode_stage_bytes(p->dec);
+    if (decode_counters(p->dec) > kCounterBytes / sizeof(WorkCounter)) {
+        delete p;
+        return GF_EINVAL;
+    }
     st = plan_alloc(p, kCounterBytes + x_total + r_total + stage);
     if (st != GF_OK) {
         delete p;

@@ -12,7 +12,7 @@ namespace gf {
 // Bytes at the start of every device workspace/plan buffer reserved for
 // self-resetting work counters (zeroed at allocation; each persistent kernel
 // returns its counters to zero when its last CTA finishes).
-constexpr size_t kCounterBytes = 256;
+constexpr size_t kCounterBytes = 8192;  // 512 counters (a blocked decode runs two batches per step)
 
 struct Workspace {
     int device = 0;

@@ -109,10 +109,11 @@ def test_uneven_batch_one_call():
 
 
 @pytest.mark.parametrize("field", [1, 8])
-@pytest.mark.parametrize("N,R", [(255, 300), (400, 420)])
+@pytest.mark.parametrize("N,R", [(255, 300), (400, 420), (400, 1700)])
 def test_large_generations(field, N, R):
-    """N = 255 keeps the rows in shared memory; N = 400 with 420 rows takes
-    the global-memory row store."""
+    """N = 255 and N = 400 take the blocked coefficient phase; N = 400 with
+    1700 rows (rows wider than the blocked phase takes) keeps the one-CTA
+    elimination with its rows in global memory."""
     g = synth.choice(71, field, N)
     src = synth.random_bytes(g, (N, 32))
     coef = synth.coefficients(g, field, (R, N), nonzero=True)
