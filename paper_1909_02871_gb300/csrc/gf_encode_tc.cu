@@ -724,10 +724,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int klo = k0i + oct * 8, khi = klo + kCodedPerHalf;  // first packet of each group of 8
             const int nlo = min(8, g.n_coded - klo), nhi = min(8, g.n_coded - khi);  // live packets
             bool ok = true;
-            for (int v = 0; v < nunits; ++v) {
-                // source chunk 0 writes (or, accumulating, adds into the output), later chunks add (XOR)
-                const bool first = v < ncols && !g.accumulate;
-                const int ct = v % ncols;
+            // source chunk 0 writes (or, accumulating, adds into the output), later chunks add (XOR)
+            bool first = !g.accumulate;
+            for (int v = 0, ct = 0; v < nunits; ++v) {
                 if (!role_wait(&ctl->d_full, tiles & 1u, abort_flag, poller, 2, kEpilogueWarps * 32)) {
                     ctl->abort = 1;
                     ok = false;
@@ -796,6 +795,10 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                     }
                 }
                 ++tiles;
+                if (++ct == ncols) {
+                    ct = 0;
+                    first = false;
+                }
             }
             if (!ok) break;
         }
