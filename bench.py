@@ -771,8 +771,9 @@ def run_fig1(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     gf.load()
     stream = torch.cuda.Stream(device=dev)
+    import oracle
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    points, launches = [], 0
+    points, launches, bit_exact = [], 0, True
     rank_barrier()
     with Clocks(local_rank) as clk:
         for field in (1, 2, 4, 8):
@@ -797,8 +798,13 @@ def run_fig1(args, rank, world, local_rank):
                 stream.synchronize()
                 ms = e0.elapsed_time(e1) / args.steps
                 gbs = G * 16 * P / (ms / 1e3) / 1e9
+                # the first and last generations of the point against the oracle
+                ok = all(np.array_equal(out[i].cpu().numpy(),
+                                        oracle.encode(field, src[i].cpu().numpy(), coef[i].cpu().numpy()))
+                         for i in (0, G - 1))
+                bit_exact = bit_exact and ok
                 points.append({"field": field, "packet_bytes": P, "generations": G, "ms": ms, "GBps_coded": gbs,
-                               "GBps_coded_per_SM": gbs / n_sm,
+                               "GBps_coded_per_SM": gbs / n_sm, "bit_exact_sampled": ok,
                                "path": {1: "table", 2: "bitsliced"}.get(path, path), "table_variant": variant})
                 launches += plan.kernel_count * args.steps
                 plan.close()
@@ -811,7 +817,8 @@ def run_fig1(args, rank, world, local_rank):
             "config": {"workload": "generations of N=16, K=16 random combinations, packet 128 B..64 KiB, GF(2), "
                                    "GF(4), GF(16), GF(256); >= 1024 generations per point (about 256 MB out)",
                        "value_is": "median over the 40 points"},
-            "points": points, "clocks": clk.summary(), "gpu_launches": launches}
+            "points": points, "clocks": clk.summary(), "gpu_launches": launches,
+            "round_trip_ok": bit_exact}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
