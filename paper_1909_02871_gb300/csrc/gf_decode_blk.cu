@@ -126,11 +126,14 @@ __global__ void __launch_bounds__(kGjThreads) blk_gj_kernel(const BlkGen *__rest
     }
     __syncthreads();
 
-    // threads share out (word j, a range of rows): per word, `per` threads split the rows; the
-    // words are taken `slots` at a time
-    const int per = max(1, kGjThreads / max(nw_r, 1));
+    // threads share out (word j, a range of rows): per word, `per` threads split the rows, `per` a
+    // power of two of at most 32 so that a word's threads lie in one warp; the words are taken
+    // `slots` at a time
+    int per = 1;
+    while (per < 32 && 2 * per * nw_r <= kGjThreads) per *= 2;
     const int slots = kGjThreads / per;
     const int wj0 = tid / per, part = tid - wj0 * per;
+    const unsigned gmask = per == 32 ? 0xffffffffu : ((1u << per) - 1u) << ((lane / per) * per);
     for (int b = 0; b < nb; ++b) {
         // pivot: first nonzero coefficient of row b (warp 0, ballot over words); the other
         // rows' values in that column are snapshotted with it
@@ -165,19 +168,18 @@ __global__ void __launch_bounds__(kGjThreads) blk_gj_kernel(const BlkGen *__rest
         __syncthreads();
         const int piv = s_piv;
         if (piv >= 0) {
-            // normalise row b (one thread per word)
+            // normalise row b and eliminate the pivot column from every other row of the block: the
+            // threads of a word each normalise it (after all of them have read the old word, one of
+            // them stores it) and apply it to their share of the rows (row b itself has g = 0)
             const ByteMap m = tab[s_inv].m;
-            for (int j = tid; j < nw_r; j += blockDim.x) cur[(size_t)b * nw + j] = apply_word(m, cur[(size_t)b * nw + j]);
-            __syncthreads();
-            // eliminate the pivot column from every other row of the block
-            if (wj0 < slots) {
-                for (int wj = wj0; wj < nw_r; wj += slots) {
-                    const Sel sel = make_sel(cur[(size_t)b * nw + wj]);
-                    for (int o = part; o < nb; o += per) {
-                        const uint32_t go = s_g[o];
-                        if (go) cur[(size_t)o * nw + wj] ^= apply(tab[go].m, sel);
-                    }
-                }
+            for (int wj = wj0; wj < nw_r; wj += slots) {
+                const uint32_t pv = apply_word(m, cur[(size_t)b * nw + wj]);
+                __syncwarp(gmask);
+                if (part == 0) cur[(size_t)b * nw + wj] = pv;
+                const Sel sel = make_sel(pv);
+                // branch-free (g = 0 maps to zero) and unrolled, so that the rows' loads overlap
+#pragma unroll 4
+                for (int o = part; o < nb; o += per) cur[(size_t)o * nw + wj] ^= apply(tab[s_g[o]].m, sel);
             }
             if (tid == 0) {
                 s_newb[s_knew] = b;
