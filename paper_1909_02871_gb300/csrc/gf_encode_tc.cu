@@ -86,7 +86,8 @@ constexpr int kDN = 256;            // MMA N: accumulator columns per pass (32 p
 constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: 64 KB)
 constexpr int kSrcPerProducer = 32;
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
-constexpr int kStageBytes = kSrcPerProducer * 32;  // 32 sources x 32 byte positions
+constexpr int kStageRow = 40;       // a staged row: the 36 aligned bytes that cover 32 positions, padded
+constexpr int kStageBytes = kSrcPerProducer * kStageRow;  // 32 sources x 32 byte positions
 // tensor memory columns (all 512 allocated)
 constexpr int kTmemCols = 512;
 constexpr int kABufCols = 64;       // A buffers at columns 0 and 64 (one column per source)
@@ -111,8 +112,8 @@ constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (eleme
 // bytes per coefficient (entry base(n) + c), from which block_row builds
 // the rows of its 8x8 block
 constexpr int kTabBase8 = 0, kTabBase4 = 256, kTabBase2 = 256 + 16, kTabBase1 = 256 + 16 + 4;
-constexpr int kTabBytes = 16 * 1024;  // 2.2 KB used; the region keeps the B halves where they were measured
-constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 24 KB source staging
+constexpr int kTabBytes = 10 * 1024;  // 2.2 KB used; the region keeps the B halves where they were measured
+constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 30 KB source staging
 constexpr int kSmemBytes = 2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*slack*/;
 
 struct Ctl {
@@ -352,30 +353,20 @@ __device__ __forceinline__ int locate(const long long *tile_start, int n_gens, l
     return lo;
 }
 
-// this producer thread's 32 source bytes of column `col` straight from
-// global memory (generations whose rows are not 4-byte aligned)
-__device__ __forceinline__ void load_direct(const EncGen &g, int ibase, unsigned long long col, uint32_t (&b)[8],
-                                            int grp)
-{
-    const unsigned long long len = g.len;
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int i = ibase + grp * 8 + t;
-        b[t] = (col < len && i < g.n_src) ? (uint32_t)__ldg(g.src + (size_t)i * len + col) : 0u;
-    }
-}
-
-// One producer lane's share of staging: the lane copies 4 bytes of rows
-// lane/8 + 4j (j = 0..7) of its warp's 32 sources, at byte positions
-// 4*(lane%8) .. +3 of its lane quarter's 32-position slice.
+// One producer lane's share of staging: the lane copies the aligned 4-byte
+// word k = lane % 8 (lane 7 also word 8) of the 36 aligned bytes that cover
+// the 32 byte positions of its lane quarter's slice, for rows lane/8 + 4j
+// (j = 0..7) of its warp's 32 sources.  Rows need not be 4-byte aligned: a
+// staged row holds its bytes from offset (row address & 3).
 struct StageLane {
-    const uint8_t *p;      // row lane/8 at column tile 0
+    const uint8_t *p;      // row lane/8 at column tile 0, the lane's 4-byte window
     const uint8_t *safe;   // any valid address (zero-size copies)
     long long stride4;     // 4 rows
-    long long col0;        // first byte position of the lane at column tile 0
+    long long col0;        // first byte position of the lane's window at column tile 0
     long long len;
     int nrows;             // rows j with a source behind them
     uint32_t soff;         // the lane's offset inside a stage
+    bool extra;            // the lane also copies word 8
 };
 
 __device__ __forceinline__ StageLane stage_lane(const EncGen &g, int ibase, int quarter, int lane)
@@ -388,25 +379,55 @@ __device__ __forceinline__ StageLane stage_lane(const EncGen &g, int ibase, int 
     s.safe = g.src;
     s.stride4 = 4 * s.len;
     s.nrows = g.n_src > r0 ? min(8, (g.n_src - r0 + 3) >> 2) : 0;
-    s.soff = (uint32_t)((lane >> 3) * 32 + 4 * (lane & 7));
+    s.soff = (uint32_t)((lane >> 3) * kStageRow + 4 * (lane & 7));
+    s.extra = (lane & 7) == 7;
     return s;
 }
 
 // Stage this warp's 32 sources x 32 byte positions of column tile `ct` into
-// shared memory with 4-byte cp.async (rows 4-byte aligned); bytes outside
-// the generation are zero-filled.
+// shared memory with 4-byte cp.async of aligned words (a misaligned row
+// takes its aligned words and one more); each copy reads only bytes of the
+// row's own range (the aligned word before a misaligned start lies in the
+// same allocation) and zero-fills the rest.
+template <bool kAligned>
 __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned char *stage)
 {
-    const long long rem = s.len - ((long long)ct * kColTile + s.col0);
-    const uint32_t bytes = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
-    const uint8_t *q = s.p + (long long)ct * kColTile;
     const uint32_t dst = smem_u32(stage) + s.soff;
+    if (kAligned) {
+        // 4-byte aligned rows: the lane's own window, one copy per row
+        const long long rem = s.len - ((long long)ct * kColTile + s.col0);
+        const uint32_t bytes = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
+        const uint8_t *q = s.p + (long long)ct * kColTile;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool live = j < s.nrows && bytes != 0u;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j),
+                         "l"(live ? q + j * s.stride4 : s.safe), "r"(live ? bytes : 0u)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const bool live = j < s.nrows && bytes != 0u;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 128 * j),
-                     "l"(live ? q + j * s.stride4 : s.safe), "r"(live ? bytes : 0u)
+        const uint8_t *a = s.p + j * s.stride4 + (long long)ct * kColTile;
+        const uint32_t m = (uint32_t)((uintptr_t)a & 3u);
+        const uint8_t *w = a - m;
+        // column of the word's first byte within its row, and the row's bytes from there
+        const long long c = (long long)ct * kColTile + s.col0 - m;
+        const long long rem = s.len - c;
+        const uint32_t b0 = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
+        const bool live = j < s.nrows;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j),
+                     "l"(live && b0 ? w : s.safe), "r"(live ? b0 : 0u)
                      : "memory");
+        if (s.extra) {
+            const long long rem1 = rem - 4;
+            const uint32_t b1 = rem1 >= 4 ? 4u : (rem1 > 0 ? (uint32_t)rem1 : 0u);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j + 4),
+                         "l"(live && b1 ? w + 4 : s.safe), "r"(live ? b1 : 0u)
+                         : "memory");
+        }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -416,6 +437,85 @@ __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned 
 __device__ __forceinline__ uint32_t b_chunk(int n, int kb, int m)
 {
     return (uint32_t)(kb * kKBlock + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
+}
+
+// What a producer warp needs to fill the A tiles of one work item.
+struct ProducerArgs {
+    const EncGen *g;
+    Ctl *ctl;
+    volatile int *abort_flag;
+    unsigned char *stage;
+    uint32_t tmem;
+    int ibase, quarter, part, lane;
+    bool poller;
+    int c0, ncols, nunits;
+    uint32_t l4, s4;  // len & 3, source address & 3
+};
+
+// The producer's units of one work item: stage the source rows kStages-1
+// tiles ahead, then for each unit wait for a free A buffer, spread the
+// source bytes into E2M1 bit values and store them into tensor memory.
+// kAligned: rows 4-byte aligned (one copy per row, bytes at offset 0).
+// Returns false if a wait gave up.
+template <bool kAligned>
+__device__ __forceinline__ bool produce_units(const ProducerArgs &pa, uint32_t &fills)
+{
+    const EncGen &g = *pa.g;
+    Ctl *ctl = pa.ctl;
+    const int lane = pa.lane, ibase = pa.ibase, ncols = pa.ncols, nunits = pa.nunits;
+    unsigned char *stage = pa.stage;
+    // always kStages-1 groups in flight before the loop (empty ones past the last unit)
+    for (int p = 0; p < kStages - 1; ++p) {
+        if (p < nunits) {
+            const int kc = p / ncols;
+            stage_tile<kAligned>(stage_lane(g, kc * kMaxSrc + ibase, pa.quarter, lane), pa.c0 + p - kc * ncols,
+                                 stage + p * kStageBytes);
+        } else {
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+    }
+    for (int v = 0; v < nunits; ++v) {
+        const int kc = v / ncols;
+        __syncwarp();  // every lane is done reading the stage about to be refilled
+        const int vs = v + kStages - 1;
+        if (vs < nunits) {
+            const int kcs = vs / ncols;
+            stage_tile<kAligned>(stage_lane(g, kcs * kMaxSrc + ibase, pa.quarter, lane), pa.c0 + vs - kcs * ncols,
+                                 stage + (vs % kStages) * kStageBytes);
+        } else {
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+        __syncwarp();
+        const uint32_t buf = fills & 1u, fu = fills >> 1;
+        if (!role_wait(&ctl->a_empty[buf], (fu & 1u) ^ 1u, pa.abort_flag, pa.poller, 3, kProducerWarps * 32))
+            return false;
+        tc_fence_after();
+        const uint32_t acol = pa.tmem + ((uint32_t)(pa.quarter * 32) << 16) + buf * kABufCols + pa.part * 32;
+        const unsigned char *sb = stage + (v % kStages) * kStageBytes + lane;
+        // misalignment of this warp's first row in the chunk; row r adds r * len
+        const uint32_t mr0 = pa.s4 + (uint32_t)(kc * kMaxSrc + ibase) * pa.l4;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint32_t w[16];
+#pragma unroll
+            for (int grp = 0; grp < 2; ++grp) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int row = (2 * half + grp) * 8 + t;
+                    const uint32_t b = kAligned ? sb[row * kStageRow] : sb[row * kStageRow + ((mr0 + (uint32_t)row * pa.l4) & 3u)];
+                    w[8 * grp + t] = spread_bits(b);
+                }
+            }
+            tmem_st16(acol + half * 16, w);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl->a_full[buf]);
+        ++fills;
+    }
+    return true;
 }
 
 // kAnyField = false: every generation of the launch is GF(256) (only that
@@ -609,7 +709,6 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         // ---------------- producers: A = source bit planes -> TMEM ----------------
         const int quarter = warp & 3;          // TMEM lane quarter
         const int part = warp >> 2;            // which 32 sources of the 64
-        const int pos = quarter * 32 + lane;   // byte position within the column tile
         const int ibase = part * kSrcPerProducer;
         unsigned char *stage = staging + warp * (kStages * kStageBytes);
         const bool poller = warp == 0;
@@ -628,72 +727,18 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->info_empty[e]);
             if (item < 0) break;
-            const bool staged = ((((uintptr_t)g.src) | (uintptr_t)g.len) & 3u) == 0;
             // units = (64-source chunk, column tile), chunk-major: the order the MMAs consume A
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
-            if (staged) {
-                // always kStages-1 groups in flight before the loop (empty ones past the last unit)
-                for (int p = 0; p < kStages - 1; ++p) {
-                    if (p < nunits) {
-                        const int kc = p / ncols;
-                        stage_tile(stage_lane(g, kc * kMaxSrc + ibase, quarter, lane), c0 + p - kc * ncols,
-                                   stage + p * kStageBytes);
-                    } else {
-                        asm volatile("cp.async.commit_group;" ::: "memory");
-                    }
-                }
+            // row r's bytes sit at offset (row address & 3) of its staged row
+            const uint32_t l4 = (uint32_t)(g.len & 3u), s4 = (uint32_t)((uintptr_t)g.src & 3u);
+            const ProducerArgs pa{&g, ctl, abort_flag, stage, tmem, ibase, quarter, part, lane, poller, c0, ncols,
+                                  nunits, l4, s4};
+            const bool ok = (l4 | s4) == 0u ? produce_units<true>(pa, fills) : produce_units<false>(pa, fills);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (!ok) {
+                ctl->abort = 1;
+                break;
             }
-            bool ok = true;
-            for (int v = 0; v < nunits; ++v) {
-                const int kc = v / ncols, ct = v - kc * ncols;
-                if (staged) {
-                    __syncwarp();  // every lane is done reading the stage about to be refilled
-                    const int vs = v + kStages - 1;
-                    if (vs < nunits) {
-                        const int kcs = vs / ncols;
-                        stage_tile(stage_lane(g, kcs * kMaxSrc + ibase, quarter, lane), c0 + vs - kcs * ncols,
-                                   stage + (vs % kStages) * kStageBytes);
-                    } else {
-                        asm volatile("cp.async.commit_group;" ::: "memory");
-                    }
-                    asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
-                    __syncwarp();
-                }
-                const uint32_t buf = fills & 1u, fu = fills >> 1;
-                if (!role_wait(&ctl->a_empty[buf], (fu & 1u) ^ 1u, abort_flag, poller, 3, kProducerWarps * 32)) {
-                    ctl->abort = 1;
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t acol = tmem + ((uint32_t)(quarter * 32) << 16) + buf * kABufCols + part * 32;
-                const unsigned char *sb = stage + (v % kStages) * kStageBytes + lane;
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t v[16];
-#pragma unroll
-                    for (int grp = 0; grp < 2; ++grp) {
-                        uint32_t b[8];
-                        if (staged) {
-#pragma unroll
-                            for (int t = 0; t < 8; ++t) b[t] = sb[((2 * half + grp) * 8 + t) * 32];
-                        } else {
-                            load_direct(g, kc * kMaxSrc + ibase, (unsigned long long)(c0 + ct) * kColTile + pos,
-                                        b, 2 * half + grp);
-                        }
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) v[8 * grp + t] = spread_bits(b[t]);
-                    }
-                    tmem_st16(acol + half * 16, v);
-                }
-                tmem_wait_st();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ctl->a_full[buf]);
-                ++fills;
-            }
-            if (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");
-            if (!ok) break;
         }
     } else if (warp < kProducerWarps + kEpilogueWarps) {
         // ---------------- epilogue: 64 D columns -> parity bytes -> global ----------------
