@@ -246,6 +246,52 @@ __device__ __forceinline__ void tc_mma_warp(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
+// The eight MMAs of one full 64-source chunk against one B half, from one
+// asm statement (one elect.sync, then an A column add, a descriptor add and
+// the MMA per step): the issuing warp shares its SM sub-partition with
+// producer and epilogue warps, and the MMAs of a pass go out measurably
+// sooner the fewer instructions it needs per MMA.  Step s reads A columns
+// a + 8s and the B K-slice at descriptor offset (s / 4) * (K-block >> 4) +
+// (s % 4) * 2 (32-byte steps within the 128-byte swizzle row).  With kBias
+// the rank-1 bias MMA that sets D to 2^23 goes first.
+#define GF_MMA_STEP(AOFF, BOFF)                                                                           \
+    "add.u32 a1, %1, " #AOFF ";\n\t"                                                                      \
+    "add.s64 b1, %2, " #BOFF ";\n\t"                                                                      \
+    "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [a1], b1, %3, [%4], [%5], p;\n\t"
+#define GF_MMA_STEPS_1_7                                                                                  \
+    GF_MMA_STEP(8, 2) GF_MMA_STEP(16, 4) GF_MMA_STEP(24, 6) GF_MMA_STEP(32, 2048) GF_MMA_STEP(40, 2050)   \
+    GF_MMA_STEP(48, 2052) GF_MMA_STEP(56, 2054)
+static_assert(kKBlock >> 4 == 2048 && kMaxSrc == 64, "the MMA steps above assume two 32 KB K-blocks of 64 sources");
+
+template <bool kBias>
+__device__ __forceinline__ void tc_mma_chunk(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t sf_a,
+                                             uint32_t sf_b, uint32_t bias_a, uint64_t bias_b, uint32_t sf_bias_a)
+{
+    if (kBias) {
+        asm volatile(
+            "{\n\t.reg .pred e, p, z;\n\t.reg .b32 r, a1;\n\t.reg .b64 b1;\n\t"
+            "elect.sync r|e, 0xffffffff;\n\t"
+            "setp.eq.b32 p, 0, 0;\n\t"
+            "setp.ne.b32 z, 0, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%6], %7, %3, [%8], [%5], z;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n\t"
+            GF_MMA_STEPS_1_7 "}" ::"r"(d),
+            "r"(a), "l"(b), "r"(idesc), "r"(sf_a), "r"(sf_b), "r"(bias_a), "l"(bias_b), "r"(sf_bias_a)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred e, p;\n\t.reg .b32 r, a1;\n\t.reg .b64 b1;\n\t"
+            "elect.sync r|e, 0xffffffff;\n\t"
+            "setp.eq.b32 p, 0, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n\t"
+            GF_MMA_STEPS_1_7 "}" ::"r"(d),
+            "r"(a), "l"(b), "r"(idesc), "r"(sf_a), "r"(sf_b)
+            : "memory");
+    }
+}
+#undef GF_MMA_STEPS_1_7
+#undef GF_MMA_STEP
+
 // 32 lanes x 16 columns of one value
 __device__ __forceinline__ void tmem_fill16(uint32_t taddr, uint32_t v)
 {
@@ -405,28 +451,27 @@ __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned 
                          "l"(live ? q + j * s.stride4 : s.safe), "r"(live ? bytes : 0u)
                          : "memory");
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint8_t *a = s.p + j * s.stride4 + (long long)ct * kColTile;
-        const uint32_t m = (uint32_t)((uintptr_t)a & 3u);
-        const uint8_t *w = a - m;
-        // column of the word's first byte within its row, and the row's bytes from there
-        const long long c = (long long)ct * kColTile + s.col0 - m;
-        const long long rem = s.len - c;
-        const uint32_t b0 = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
-        const bool live = j < s.nrows;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j),
-                     "l"(live && b0 ? w : s.safe), "r"(live ? b0 : 0u)
-                     : "memory");
-        if (s.extra) {
-            const long long rem1 = rem - 4;
-            const uint32_t b1 = rem1 >= 4 ? 4u : (rem1 > 0 ? (uint32_t)rem1 : 0u);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j + 4),
-                         "l"(live && b1 ? w + 4 : s.safe), "r"(live ? b1 : 0u)
+        for (int j = 0; j < 8; ++j) {
+            const uint8_t *a = s.p + j * s.stride4 + (long long)ct * kColTile;
+            const uint32_t m = (uint32_t)((uintptr_t)a & 3u);
+            const uint8_t *w = a - m;
+            // column of the word's first byte within its row, and the row's bytes from there
+            const long long c = (long long)ct * kColTile + s.col0 - m;
+            const long long rem = s.len - c;
+            const uint32_t b0 = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
+            const bool live = j < s.nrows;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j),
+                         "l"(live && b0 ? w : s.safe), "r"(live ? b0 : 0u)
                          : "memory");
+            if (s.extra) {
+                const long long rem1 = rem - 4;
+                const uint32_t b1 = rem1 >= 4 ? 4u : (rem1 > 0 ? (uint32_t)rem1 : 0u);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j + 4),
+                             "l"(live && b1 ? w + 4 : s.safe), "r"(live ? b1 : 0u)
+                             : "memory");
+            }
         }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -768,6 +813,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const int nunits = (g.n_src + kMaxSrc - 1) / kMaxSrc * ncols;
             const int klo = k0i + oct * 8, khi = klo + kCodedPerHalf;  // first packet of each group of 8
             const int nlo = min(8, g.n_coded - klo), nhi = min(8, g.n_coded - khi);  // live packets
+            // rows of 4-byte aligned words: each lane stores whole words (see below)
+            const bool wide = ((len & 3ull) | ((uintptr_t)g.out & 3u)) == 0;
             bool ok = true;
             // source chunk 0 writes (or, accumulating, adds into the output), later chunks add (XOR)
             bool first = !g.accumulate;
@@ -801,7 +848,42 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                         ob[2] |= h0 << (8 * t); ob[3] |= h1 << (8 * t);
                     }
                 }
-                if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nlo > 0) {
+                if (wide) {
+                    // A byte transpose within each quad of lanes (two exchanges: bytes with lane ^ 1,
+                    // halfwords with lane ^ 2) turns the quad's four words of packets 4m..4m+3 at one
+                    // position each into lane j's word of packet 4m+j at the quad's four positions, so
+                    // one 4-byte store replaces four byte stores.
+                    const size_t at = (size_t)(c0 + ct) * kColTile + (size_t)(pos & ~3);
+                    // byte selectors: even/odd bytes with lane ^ 1, then low/high halfwords with lane ^ 2
+                    const uint32_t sel1 = (lane & 1) ? 0x3715u : 0x6240u, sel2 = (lane & 2) ? 0x3276u : 0x5410u;
+                    uint32_t wv[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t z = __byte_perm(ob[m], __shfl_xor_sync(0xffffffffu, ob[m], 1), sel1);
+                        wv[m] = __byte_perm(z, __shfl_xor_sync(0xffffffffu, z, 2), sel2);
+                    }
+                    if (at < len && nlo > 0) {
+                        // lane j's packets: klo + j + {0, 4} and khi + j + {0, 4} (khi = klo + 32)
+                        uint8_t *o = g.out + (size_t)(klo + (lane & 3)) * len + at;
+                        const int rel = g.n_coded - klo - (lane & 3);  // live while the offset is below it
+                        if (!first) {
+                            // a later source chunk adds its share (loads issued before the stores)
+                            uint32_t old[4];
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) {
+                                const int d = 32 * (m >> 1) + 4 * (m & 1);
+                                old[m] = d < rel ? *reinterpret_cast<const uint32_t *>(o + (size_t)d * len) : 0u;
+                            }
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) wv[m] ^= old[m];
+                        }
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int d = 32 * (m >> 1) + 4 * (m & 1);
+                            if (d < rel) *reinterpret_cast<uint32_t *>(o + (size_t)d * len) = wv[m];
+                        }
+                    }
+                } else if ((unsigned long long)(c0 + ct) * kColTile + pos < len && nlo > 0) {
                     // two groups of 8 packets (lo, hi), one pointer walked down each group's rows
 #pragma unroll
                     for (int grp = 0; grp < 2; ++grp) {
@@ -889,12 +971,18 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 const uint32_t dt = tmem + kDCol0;
                 // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field: B
                 // lies below 256 KB of shared memory)
-                tc_mma_warp(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
+                if (ksteps == 8) {
+                    tc_mma_chunk<true>(dt, at, bdesc_lo, kIdesc, tmem + kSfOneA, tmem + kSfOneB, tmem + kBiasACol,
+                                       bias_desc, tmem + kSfBiasA);
+                } else {
+                    tc_mma_warp(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    if (s < ksteps)
-                        tc_mma_warp(dt, at + s * 8, bdesc_lo + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4),
-                                    kIdesc, tmem + kSfOneA, tmem + kSfOneB, 1u);
+                    for (int s = 0; s < 7; ++s) {
+                        if (s < ksteps)
+                            tc_mma_warp(dt, at + s * 8,
+                                        bdesc_lo + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
+                                        tmem + kSfOneA, tmem + kSfOneB, 1u);
+                    }
                 }
                 if (ct == ncols - 1) {
                     tc_commit_warp(&ctl->b_empty[0]);  // the lo half is free for the next item
@@ -906,12 +994,16 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                         ok = false;
                         break;
                     }
+                    if (ksteps == 8) {
+                        tc_mma_chunk<false>(dt, at, bdesc_hi, kIdesc, tmem + kSfOneA, tmem + kSfHiB, 0u, 0ull, 0u);
+                    } else {
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        if (s < ksteps)
-                            tc_mma_warp(dt, at + s * 8,
-                                        bdesc_hi + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
-                                        tmem + kSfOneA, tmem + kSfHiB, 1u);
+                        for (int s = 0; s < 7; ++s) {
+                            if (s < ksteps)
+                                tc_mma_warp(dt, at + s * 8,
+                                            bdesc_hi + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
+                                            tmem + kSfOneA, tmem + kSfHiB, 1u);
+                        }
                     }
                 }
                 tc_commit_warp(&ctl->d_full);
