@@ -23,10 +23,11 @@
 //     warps straight into tensor memory with tcgen05.st (one TMEM lane per
 //     byte position, one column = the 8 bit values of one source byte);
 //   B (K = 2 x 8N: the bit matrices of packets 0..31 of the item, then those
-//     of packets 32..63, x N = 256 columns): K-major, 128-byte swizzled, two
-//     halves of 64 KB in shared memory (64 sources each; the lo and the hi
-//     packets), built from a per-CTA table of the 8x8 blocks of every
-//     coefficient.  The MMAs over the hi half reuse the same A columns and
+//     of packets 32..63, x N = 256 columns): K-major, 128-byte swizzled, in
+//     K-blocks of 32 sources (32 KB each: lo K-blocks 0 and 1, then hi
+//     K-blocks 0 and 1 per 64-source chunk), built from a per-CTA table of
+//     the coefficients' unit images into a ring of five K-block buffers in
+//     shared memory.  The MMAs over the hi half reuse the same A columns and
 //     take block scale 2^10 for B (UE8M0 137);
 //   D (128 lanes x 256 FP32 columns): one pass of 17 MMAs (N = 256) covers
 //     all 64 coded packets of the item.  (An MMA costs about 95 SM clocks
@@ -45,17 +46,20 @@
 // tile feeds one D pass (so the source bit planes are built once per 64
 // coded packets).  The first chunk's passes write the coded bytes,
 // later chunks' passes XOR into them (the same thread owns the same bytes).  Roles, all running
-// concurrently: 4 warps publish the next item in a two-entry ring and build
-// each half of its B as soon as the previous item's last pass over that half
-// is done; 8 producer warps stage their source rows in shared memory with
-// cp.async two tiles ahead and fill A (double-buffered in TMEM, via a 1 KB
-// bit spread computed in registers); 1 warp issues the MMAs (converged, one
-// elected lane issues; an MMA's issue holds the warp until the tensor pipe
-// takes it, so the warp does nothing else); 16 epilogue warps drain D and
-// release each A buffer once the D of its pass has landed; the B builders
-// rebuild each half for the next item as soon as the MMAs of the item's
-// last pass over that half are complete (a commit between the lo and the
-// hi MMAs).  Handshakes arrive once per warp
+// concurrently: 4 warps publish the next item in a two-entry ring (and start
+// its first source tiles and its coefficients on their way into L2), then
+// build its B K-blocks, each into the next slot of the K-block ring: a pass
+// reads at most four, so the next item's first K-block is built while the
+// current item still runs, and each later one as soon as the MMAs of the
+// current item's last pass are done with the slot it takes over (a commit
+// after each K-block's MMAs of a chunk's last tile); 8 producer warps stage
+// their source rows in shared memory with cp.async two tiles ahead and fill
+// A (double-buffered in TMEM, via a 1 KB bit spread computed in registers);
+// 1 warp issues the MMAs (converged, one elected lane issues each group of
+// four from one asm statement; an MMA's issue holds the warp until the
+// tensor pipe takes it, so the warp does nothing else); 16 epilogue warps
+// drain D and release each A buffer once the D of its pass has landed.
+// Handshakes arrive once per warp
 // (after __syncwarp).  A role of several warps waits through one polling
 // warp while the others are parked on a named barrier, which also hands
 // every warp the same outcome.  Every mbarrier wait is bounded by the global
@@ -83,11 +87,16 @@ constexpr int kColTile = 128;       // byte positions per tile (MMA M)
 constexpr int kCodedPerItem = 64;   // coded packets per work item: two halves
 constexpr int kCodedPerHalf = 32;   // coded packets of one B half (lo: bit 0, hi: bit 10 of the sums)
 constexpr int kDN = 256;            // MMA N: accumulator columns per pass (32 packet slots x 8 bits)
-constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: 64 KB)
-constexpr int kSrcPerProducer = 32;
+constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: two 32 KB K-blocks)
+constexpr int kSrcPerProducer = kMaxSrc * 4 / kProducerWarps;  // sources of a chunk per producer warp
+constexpr int kRowGroups = kSrcPerProducer / 4;  // a staging copy covers 4 rows (8 lanes each)
 constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
 constexpr int kStageRow = 40;       // a staged row: the 36 aligned bytes that cover 32 positions, padded
-constexpr int kStageBytes = kSrcPerProducer * kStageRow;  // 32 sources x 32 byte positions
+constexpr int kStageBytes = kSrcPerProducer * kStageRow;  // the warp's sources x 32 byte positions
+constexpr int kBThreads = kBWarps * 32;
+constexpr int kBPkt = kCodedPerHalf * 8 / kBThreads;  // coded packets per builder thread and K-block
+static_assert(kProducerWarps % 4 == 0 && kSrcPerProducer % 16 == 0, "producer warps cover whole lane quarters");
+static_assert(kBThreads % 8 == 0 && kBPkt >= 1 && kCodedPerHalf % kBPkt == 0, "builder thread split");
 // tensor memory columns (all 512 allocated)
 constexpr int kTmemCols = 512;
 constexpr int kABufCols = 64;       // A buffers at columns 0 and 64 (one column per source)
@@ -106,19 +115,21 @@ constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
 constexpr int kKBlock = kDN * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
-constexpr int kBBytes = 2 * kKBlock;        // 64 KB: one B half (K <= 512, 32 coded packets)
+constexpr int kBSlots = 5;                  // K-block buffers in a ring (a pass reads up to 4)
 constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
 // The unit images of every coefficient of GF(256), GF(16), GF(4), GF(2): 8
 // bytes per coefficient (entry base(n) + c), from which block_row builds
 // the rows of its 8x8 block
 constexpr int kTabBase8 = 0, kTabBase4 = 256, kTabBase2 = 256 + 16, kTabBase1 = 256 + 16 + 4;
-constexpr int kTabBytes = 10 * 1024;  // 2.2 KB used; the region keeps the B halves where they were measured
+constexpr int kTabBytes = 3 * 1024;   // 278 entries of 8 bytes
 constexpr int kStageAll = kProducerWarps * kStages * kStageBytes;  // 30 KB source staging
-constexpr int kSmemBytes = 2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*slack*/;
+constexpr int kSmemBytes = kBSlots * kKBlock + kBiasBBytes + kTabBytes + kStageAll + 1024 /*control*/ + 1024 /*slack*/;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
 
 struct Ctl {
     unsigned long long a_full[2], a_empty[2], d_full, d_empty;
-    unsigned long long info_full[2], info_empty[2], b_full[2], b_empty[2], drain;
+    unsigned long long info_full[2], info_empty[2], drain;
+    unsigned long long b_full[kBSlots], b_empty[kBSlots];  // the K-block buffer ring
     long long ring_item[2];
     EncGen ring_gen[2];  // generation record of each published item
     int ring_k0[2];      // its first coded packet
@@ -129,7 +140,7 @@ struct Ctl {
 
 static_assert(sizeof(Ctl) <= 1024, "control block (below the B halves)");
 static_assert((kBiasBBytes + kTabBytes + kStageAll + 1024) % 1024 == 0, "B halves 1024-aligned");
-static_assert(2 * kBBytes + kBiasBBytes + kTabBytes + kStageAll + 1024 + 1023 <= kSmemBytes, "shared memory");
+static_assert(kBSlots * kKBlock + kBiasBBytes + kTabBytes + kStageAll + 1024 + 1023 <= kSmemBytes, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -246,26 +257,24 @@ __device__ __forceinline__ void tc_mma_warp(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
-// The eight MMAs of one full 64-source chunk against one B half, from one
-// asm statement (one elect.sync, then an A column add, a descriptor add and
-// the MMA per step): the issuing warp shares its SM sub-partition with
-// producer and epilogue warps, and the MMAs of a pass go out measurably
-// sooner the fewer instructions it needs per MMA.  Step s reads A columns
-// a + 8s and the B K-slice at descriptor offset (s / 4) * (K-block >> 4) +
-// (s % 4) * 2 (32-byte steps within the 128-byte swizzle row).  With kBias
-// the rank-1 bias MMA that sets D to 2^23 goes first.
+// The four MMAs of one full 32-source K-block, from one asm statement (one
+// elect.sync, then an A column add, a descriptor add and the MMA per step):
+// the issuing warp shares its SM sub-partition with producer and epilogue
+// warps, and the MMAs of a pass go out measurably sooner the fewer
+// instructions it needs per MMA.  Step s reads A columns a + 8s and the B
+// K-slice at descriptor offset 2s (32-byte steps within the 128-byte
+// swizzle row).  With kBias the rank-1 bias MMA that sets D to 2^23 goes
+// first.
 #define GF_MMA_STEP(AOFF, BOFF)                                                                           \
     "add.u32 a1, %1, " #AOFF ";\n\t"                                                                      \
     "add.s64 b1, %2, " #BOFF ";\n\t"                                                                      \
     "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [a1], b1, %3, [%4], [%5], p;\n\t"
-#define GF_MMA_STEPS_1_7                                                                                  \
-    GF_MMA_STEP(8, 2) GF_MMA_STEP(16, 4) GF_MMA_STEP(24, 6) GF_MMA_STEP(32, 2048) GF_MMA_STEP(40, 2050)   \
-    GF_MMA_STEP(48, 2052) GF_MMA_STEP(56, 2054)
-static_assert(kKBlock >> 4 == 2048 && kMaxSrc == 64, "the MMA steps above assume two 32 KB K-blocks of 64 sources");
+#define GF_MMA_STEPS_1_3 GF_MMA_STEP(8, 2) GF_MMA_STEP(16, 4) GF_MMA_STEP(24, 6)
+static_assert(kKBlock == 32 * 1024 && kMaxSrc == 64, "K-blocks of 32 sources, 128-byte rows");
 
 template <bool kBias>
-__device__ __forceinline__ void tc_mma_chunk(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t sf_a,
-                                             uint32_t sf_b, uint32_t bias_a, uint64_t bias_b, uint32_t sf_bias_a)
+__device__ __forceinline__ void tc_mma_quad(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t sf_a,
+                                            uint32_t sf_b, uint32_t bias_a, uint64_t bias_b, uint32_t sf_bias_a)
 {
     if (kBias) {
         asm volatile(
@@ -275,7 +284,7 @@ __device__ __forceinline__ void tc_mma_chunk(uint32_t d, uint32_t a, uint64_t b,
             "setp.ne.b32 z, 0, 0;\n\t"
             "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%6], %7, %3, [%8], [%5], z;\n\t"
             "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n\t"
-            GF_MMA_STEPS_1_7 "}" ::"r"(d),
+            GF_MMA_STEPS_1_3 "}" ::"r"(d),
             "r"(a), "l"(b), "r"(idesc), "r"(sf_a), "r"(sf_b), "r"(bias_a), "l"(bias_b), "r"(sf_bias_a)
             : "memory");
     } else {
@@ -284,12 +293,12 @@ __device__ __forceinline__ void tc_mma_chunk(uint32_t d, uint32_t a, uint64_t b,
             "elect.sync r|e, 0xffffffff;\n\t"
             "setp.eq.b32 p, 0, 0;\n\t"
             "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n\t"
-            GF_MMA_STEPS_1_7 "}" ::"r"(d),
+            GF_MMA_STEPS_1_3 "}" ::"r"(d),
             "r"(a), "l"(b), "r"(idesc), "r"(sf_a), "r"(sf_b)
             : "memory");
     }
 }
-#undef GF_MMA_STEPS_1_7
+#undef GF_MMA_STEPS_1_3
 #undef GF_MMA_STEP
 
 // 32 lanes x 16 columns of one value
@@ -358,12 +367,15 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t b)
 }
 
 // Row r of a coefficient's 8x8 block in the same K order: nibble 2i is bit r
-// of p_i and nibble 2i + 1 bit r of p_(i+4), where p_j (byte j of the pair
-// P: bytes 0..3 in .x, 4..7 in .y) is the image of the unit byte with bit j
-// set under the coefficient's map.
-__device__ __forceinline__ uint32_t block_row(uint2 P, int r)
+// of p_i and nibble 2i + 1 bit r of p_(i+4), where p_j is the image of the
+// unit byte with bit j set under the coefficient's map.  The table holds the
+// images as nibble planes Z: nibble s of Z.x is the low nibble and nibble s
+// of Z.y the high nibble of the image that nibble s of a row takes its bit
+// from (p_(s/2) for even s, p_(4+s/2) for odd s), so row r is bit r % 4 of
+// every nibble of one plane moved to bit 1 (E2M1 1.0): a shift and a mask.
+__device__ __forceinline__ uint32_t block_row(uint2 Z, int r)
 {
-    return ((((P.x >> r) & 0x01010101u) | (((P.y >> r) & 0x01010101u) << 4)) << 1);
+    return (((r < 4 ? Z.x : Z.y) >> (r & 3)) & 0x11111111u) << 1;
 }
 
 // parity byte of 8 biased sums, low 16 bits packed two per word (word j =
@@ -402,7 +414,7 @@ __device__ __forceinline__ int locate(const long long *tile_start, int n_gens, l
 // One producer lane's share of staging: the lane copies the aligned 4-byte
 // word k = lane % 8 (lane 7 also word 8) of the 36 aligned bytes that cover
 // the 32 byte positions of its lane quarter's slice, for rows lane/8 + 4j
-// (j = 0..7) of its warp's 32 sources.  Rows need not be 4-byte aligned: a
+// (j < kRowGroups) of its warp's sources.  Rows need not be 4-byte aligned: a
 // staged row holds its bytes from offset (row address & 3).
 struct StageLane {
     const uint8_t *p;      // row lane/8 at column tile 0, the lane's 4-byte window
@@ -424,7 +436,7 @@ __device__ __forceinline__ StageLane stage_lane(const EncGen &g, int ibase, int 
     s.p = g.src + (size_t)r0 * g.len + s.col0;
     s.safe = g.src;
     s.stride4 = 4 * s.len;
-    s.nrows = g.n_src > r0 ? min(8, (g.n_src - r0 + 3) >> 2) : 0;
+    s.nrows = g.n_src > r0 ? min(kRowGroups, (g.n_src - r0 + 3) >> 2) : 0;
     s.soff = (uint32_t)((lane >> 3) * kStageRow + 4 * (lane & 7));
     s.extra = (lane & 7) == 7;
     return s;
@@ -445,7 +457,7 @@ __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned 
         const uint32_t bytes = rem >= 4 ? 4u : (rem > 0 ? (uint32_t)rem : 0u);
         const uint8_t *q = s.p + (long long)ct * kColTile;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kRowGroups; ++j) {
             const bool live = j < s.nrows && bytes != 0u;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst + 4 * kStageRow * j),
                          "l"(live ? q + j * s.stride4 : s.safe), "r"(live ? bytes : 0u)
@@ -453,7 +465,7 @@ __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned 
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kRowGroups; ++j) {
             const uint8_t *a = s.p + j * s.stride4 + (long long)ct * kColTile;
             const uint32_t m = (uint32_t)((uintptr_t)a & 3u);
             const uint8_t *w = a - m;
@@ -477,11 +489,12 @@ __device__ __forceinline__ void stage_tile(const StageLane &s, int ct, unsigned 
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Shared-memory offset of 16-byte chunk m of K-block kb in B row n (K-major,
-// 128-byte swizzle: 8-row atoms of 1024 bytes, chunk index XOR row % 8).
-__device__ __forceinline__ uint32_t b_chunk(int n, int kb, int m)
+// Shared-memory offset of 16-byte chunk m of B row n within a K-block
+// buffer (K-major, 128-byte swizzle: 8-row atoms of 1024 bytes, chunk index
+// XOR row % 8).
+__device__ __forceinline__ uint32_t b_chunk(int n, int m)
 {
-    return (uint32_t)(kb * kKBlock + (n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
+    return (uint32_t)((n >> 3) * 1024 + (n & 7) * 128 + ((m ^ (n & 7)) << 4));
 }
 
 // What a producer warp needs to fill the A tiles of one work item.
@@ -536,12 +549,12 @@ __device__ __forceinline__ bool produce_units(const ProducerArgs &pa, uint32_t &
         if (!role_wait(&ctl->a_empty[buf], (fu & 1u) ^ 1u, pa.abort_flag, pa.poller, 3, kProducerWarps * 32))
             return false;
         tc_fence_after();
-        const uint32_t acol = pa.tmem + ((uint32_t)(pa.quarter * 32) << 16) + buf * kABufCols + pa.part * 32;
+        const uint32_t acol = pa.tmem + ((uint32_t)(pa.quarter * 32) << 16) + buf * kABufCols + pa.part * kSrcPerProducer;
         const unsigned char *sb = stage + (v % kStages) * kStageBytes + lane;
         // misalignment of this warp's first row in the chunk; row r adds r * len
         const uint32_t mr0 = pa.s4 + (uint32_t)(kc * kMaxSrc + ibase) * pa.l4;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
+        for (int half = 0; half < kSrcPerProducer / 16; ++half) {
             uint32_t w[16];
 #pragma unroll
             for (int grp = 0; grp < 2; ++grp) {
@@ -574,13 +587,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // the bias operand, tables, staging and control first, the two B halves above them (with a B
-    // half at the bottom of shared memory its MMAs ran about a third slower, measured)
+    // the bias operand, tables, staging and control first, the K-block ring above them (with B at
+    // the bottom of shared memory its MMAs ran about a third slower, measured)
     unsigned char *bias_b = smem;
-    uint2 *tab = reinterpret_cast<uint2 *>(bias_b + kBiasBBytes);  // [field][c]: unit images
+    uint2 *tab = reinterpret_cast<uint2 *>(bias_b + kBiasBBytes);  // [field][c]: nibble planes of the unit images
     unsigned char *staging = reinterpret_cast<unsigned char *>(tab) + kTabBytes;
     Ctl *ctl = reinterpret_cast<Ctl *>(staging + kStageAll);
-    unsigned char *Bs = staging + kStageAll + 1024;                  // two B buffers (1024-aligned)
+    unsigned char *Bs = staging + kStageAll + 1024;                  // the K-block ring (1024-aligned)
     volatile int *abort_flag = &ctl->abort;
     volatile long long *ring = ctl->ring_item;
 
@@ -593,10 +606,13 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     for (int e = tid; e < 256 + (kAnyField ? 22 : 0); e += blockDim.x) {
         const int n = e < kTabBase4 ? 8 : e < kTabBase2 ? 4 : e < kTabBase1 ? 2 : 1;
         const uint32_t c = (uint32_t)(e - (n == 8 ? kTabBase8 : n == 4 ? kTabBase4 : n == 2 ? kTabBase2 : kTabBase1));
-        uint2 P;
-        P.x = unit_image(n, c, 0) | (unit_image(n, c, 1) << 8) | (unit_image(n, c, 2) << 16) | (unit_image(n, c, 3) << 24);
-        P.y = unit_image(n, c, 4) | (unit_image(n, c, 5) << 8) | (unit_image(n, c, 6) << 16) | (unit_image(n, c, 7) << 24);
-        tab[e] = P;
+        uint2 Z = make_uint2(0u, 0u);
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t p = unit_image(n, c, (t & 1) * 4 + (t >> 1));  // the image nibble t reads
+            Z.x |= (p & 0xFu) << (4 * t);
+            Z.y |= (p >> 4) << (4 * t);
+        }
+        tab[e] = Z;
     }
     // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
     for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x) {
@@ -612,6 +628,8 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             mbar_init(&ctl->a_empty[b], 1);
             mbar_init(&ctl->info_full[b], 1);
             mbar_init(&ctl->info_empty[b], kProducerWarps + kEpilogueWarps + 1);
+        }
+        for (int b = 0; b < kBSlots; ++b) {
             mbar_init(&ctl->b_full[b], 1);
             mbar_init(&ctl->b_empty[b], 1);
         }
@@ -655,10 +673,11 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     if (warp >= kBWarp0) {
         // ------------- B builder: publishes the next item, then its bit matrices -------------
         const int bt = tid - kBWarp0 * 32;
-        const int m = bt & 7;            // 16-byte chunk of a K-block: sources 4m .. 4m+3
-        const int kb = (bt >> 3) & 1;    // K-block: sources 32kb .. 32kb+31
-        const int kq = bt >> 4;          // coded packets 4kq .. 4kq+3 of a half
-        uint32_t bfills0 = 0, bfills1 = 0;  // fills of each B half so far
+        const int m = bt & 7;            // 16-byte chunk of a K-block row: sources 4m .. 4m+3 of the K-block
+        const int kq = bt >> 3;          // coded packets kBPkt kq .. kBPkt kq + kBPkt-1 of a half
+        // the ring slot of the next K-block unit and, per slot, the parity of its next fill
+        int bslot = 0;
+        uint32_t bpar = 0;
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (bt == 0) {
@@ -699,43 +718,87 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 kAnyField ? tab + (field == 8 ? kTabBase8 : field == 4 ? kTabBase4 : field == 2 ? kTabBase2 : kTabBase1)
                           : tab;
             const int nh = (min(kCodedPerItem, K - ctl->ring_k0[e]) + kCodedPerHalf - 1) / kCodedPerHalf;
-            bool stop = false;
-            // one B half per (source chunk kc, half h), in the order the MMAs consume them
-            for (int u = 0; u < nkc * nh; ++u) {
-                const int kc = nh == 2 ? u >> 1 : u, h = nh == 2 ? u & 1 : 0;
+            {
+                // The producers stage the item's first column tiles right at the item boundary: start
+                // them on their way into L2 now (an item ahead), one 128-byte line per thread, both
+                // lines a tile may straddle, first source chunk.
+                const int row = bt >> 2, tile = (bt >> 1) & 1, line = bt & 1;
+                const int c0 = kColSplit ? ctl->ring_c0[e] : 0;
+                const unsigned long long off = (unsigned long long)(c0 + tile) * kColTile + line * (kColTile - 1);
+                if (row < min(N, kMaxSrc) && off < g.len)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(g.src + (size_t)row * g.len + off));
+                // and the item's coefficient rows, which the builders read unit by unit
+                const int nk = min(kCodedPerItem, K - ctl->ring_k0[e]), nl = (N + 127) / 128 + 1;
+                for (int j = bt; j < nk * nl; j += kBThreads) {
+                    const int k = j / nl;
+                    const size_t o = min((size_t)(j - k * nl) * 128, (size_t)N - 1);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(coef + (size_t)(ctl->ring_k0[e] + k) * ld + o));
+                }
+            }
+            // Units (source chunk kc, half h, K-block kb) in the order the MMAs consume them, each
+            // built into the next slot of a ring of kBSlots 32 KB K-block buffers: a pass reads at
+            // most four, so the next item's first K-block is built while the current item runs,
+            // and each later one as soon as the MMAs are done with the slot it takes over.
+            const int nunit = nkc * nh * 2;
+            auto unit_of = [&](int u, int &kc, int &h, int &kb) {
+                kb = u & 1;
+                kc = nh == 2 ? u >> 2 : u >> 1;
+                h = nh == 2 ? (u >> 1) & 1 : 0;
+            };
+            // coefficients c[k][i0 .. i0+3] of the thread's packets in unit u, one byte each (one
+            // 4-byte load when the rows are 4-byte aligned: i0 is a multiple of 4)
+            const bool cc_words = ((ld | (int)((uintptr_t)coef & 3u)) & 3) == 0;
+            auto load_cc = [&](int u, uint32_t *cc) {
+                int kc, h, kb;
+                unit_of(u, kc, h, kb);
                 const int i0 = kMaxSrc * kc + 32 * kb + 4 * m;
-                const int nkb = (min(kMaxSrc, N - kMaxSrc * kc) + 31) / 32;
                 const int kbase = ctl->ring_k0[e] + h * kCodedPerHalf;
-                uint32_t cc[4];  // coefficients c[k][i0 .. i0+3], one byte each
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int k = kbase + kq * 4 + t;
+                for (int t = 0; t < kBPkt; ++t) {
+                    const int k = kbase + kq * kBPkt + t;
+                    const uint8_t *q = coef + (size_t)k * ld + i0;
                     uint32_t w = 0;
+                    if (k < K && i0 + 3 < N && cc_words) {
+                        w = __ldg(reinterpret_cast<const uint32_t *>(q));
+                    } else {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (kb < nkb && k < K && i0 + u < N)
-                            w |= (uint32_t)__ldg(coef + (size_t)k * ld + i0 + u) << (8 * u);
+                        for (int x = 0; x < 4; ++x)
+                            if (k < K && i0 + x < N) w |= (uint32_t)__ldg(q + x) << (8 * x);
+                    }
                     cc[t] = w;
                 }
-                // wait until the MMAs of the previous item are done with this half
-                unsigned char *Bb = Bs + h * kBBytes;
-                if (bt == 0 && !mbar_wait(&ctl->b_empty[h], ((h ? bfills1 : bfills0) & 1u) ^ 1u, abort_flag))
+            };
+            uint32_t ccn[kBPkt];
+            load_cc(0, ccn);
+            bool stop = false;
+            for (int u = 0; u < nunit; ++u) {
+                int kc, h, kb;
+                unit_of(u, kc, h, kb);
+                const int nkb = (min(kMaxSrc, N - kMaxSrc * kc) + 31) / 32;  // K-blocks with sources
+                uint32_t cc[kBPkt];
+#pragma unroll
+                for (int t = 0; t < kBPkt; ++t) cc[t] = ccn[t];
+                if (u + 1 < nunit) load_cc(u + 1, ccn);  // in flight while this unit waits and builds
+                // wait until the MMAs are done with what the slot held before
+                const int x = bslot;
+                unsigned char *Bb = Bs + x * kKBlock;
+                if (bt == 0 && !mbar_wait(&ctl->b_empty[x], ((bpar >> x) & 1u) ^ 1u, abort_flag))
                     ctl->abort = 1;
                 asm volatile("bar.sync 1, %0;" ::"r"(kBWarps * 32) : "memory");
                 if (kb < nkb) {
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int kp = kq * 4 + t;  // packet of the half = column slot
+                    for (int t = 0; t < kBPkt; ++t) {
+                        const int kp = kq * kBPkt + t;  // packet of the half = column slot
                         const uint32_t w = cc[t];
-                        // unit images of the 4 coefficients (sources 4m .. 4m + 3), then the 8 rows
+                        // nibble planes of the 4 coefficients (sources 4m .. 4m + 3), then the 8 rows
                         uint2 P[4];
 #pragma unroll
-                        for (int x = 0; x < 4; ++x) P[x] = ftab[(w >> (8 * x)) & 0xFFu];
+                        for (int y = 0; y < 4; ++y) P[y] = ftab[(w >> (8 * y)) & 0xFFu];
 #pragma unroll
                         for (int r = 0; r < 8; ++r) {
                             const uint4 q = make_uint4(block_row(P[0], r), block_row(P[1], r), block_row(P[2], r),
                                                        block_row(P[3], r));
-                            *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, kb, m)) = q;
+                            *reinterpret_cast<uint4 *>(Bb + b_chunk(8 * kp + r, m)) = q;
                         }
                     }
                 }
@@ -743,9 +806,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 // one decision for all builder threads (a per-thread read of the flag could
                 // split them across the next named barrier)
                 stop = bar_or(1, kBWarps * 32, *abort_flag != 0);
-                if (bt == 0) mbar_arrive(&ctl->b_full[h]);
-                if (h) ++bfills1;
-                else ++bfills0;
+                if (bt == 0) mbar_arrive(&ctl->b_full[x]);
+                bpar ^= 1u << x;
+                bslot = x + 1 == kBSlots ? 0 : x + 1;
                 if (stop) break;
             }
             if (stop) break;
@@ -753,7 +816,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
     } else if (warp < kProducerWarps) {
         // ---------------- producers: A = source bit planes -> TMEM ----------------
         const int quarter = warp & 3;          // TMEM lane quarter
-        const int part = warp >> 2;            // which 32 sources of the 64
+        const int part = warp >> 2;            // which sources of the 64 (kSrcPerProducer from part * it)
         const int ibase = part * kSrcPerProducer;
         unsigned char *stage = staging + warp * (kStages * kStageBytes);
         const bool poller = warp == 0;
@@ -933,12 +996,15 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         // ---------------- MMA issuer (warp kMmaWarp; one elected lane issues) ----------------
         // The whole warp runs the loop and waits together (a lone looping lane whose
         // warp-mates sit at the final __syncthreads issues markedly slower).  One pass per
-        // unit: the bias MMA, the lo MMAs (B half 0), the hi MMAs (B half 1, block scale
-        // 2^10).  A buffers are released by the epilogue once the pass's D has landed.
+        // unit: the bias MMA, the lo MMAs (two K-blocks), the hi MMAs (two K-blocks, block
+        // scale 2^10).  A buffers are released by the epilogue once the pass's D has landed.
         uint32_t fills = 0, tiles = 0;
-        uint32_t bused0 = 0, bused1 = 0;  // fills of each B half consumed so far
+        // ring slot of the current chunk's first K-block unit and, per slot, the parity of the
+        // fill being consumed
+        int bslot = 0;
+        uint32_t bpar = 0;
         const uint64_t bias_desc = b_desc(smem_u32(bias_b));
-        const uint64_t bdesc_lo = b_desc(smem_u32(Bs)), bdesc_hi = b_desc(smem_u32(Bs + kBBytes));
+        const uint64_t bdesc0 = b_desc(smem_u32(Bs));  // slot x: + x * (K-block >> 4)
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
             if (!warp_wait(&ctl->info_full[e], use & 1u, abort_flag)) {
@@ -956,12 +1022,30 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
             const bool hi = g.n_coded - k0i > kCodedPerHalf;  // the item has packets in the hi half
             bool ok = true;
             int ct = 0, i0 = 0;  // column tile, first source of the 64-source chunk
+            // the MMAs of one K-block (slot x): the asm quad when the chunk fills it, else one by one
+            auto kblock = [&](int kb, int ksteps, uint32_t at, uint32_t dt, int x, uint32_t sf_b) {
+                const uint32_t a0 = at + 32 * kb;
+                const uint64_t b0 = bdesc0 + (uint64_t)((x * kKBlock) >> 4);
+                if (ksteps >= 4 * kb + 4) {
+                    tc_mma_quad<false>(dt, a0, b0, kIdesc, tmem + kSfOneA, sf_b, 0u, 0ull, 0u);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+                        if (4 * kb + s < ksteps)
+                            tc_mma_warp(dt, a0 + 8 * s, b0 + (uint64_t)(2 * s), kIdesc, tmem + kSfOneA, sf_b, 1u);
+                }
+            };
+            auto slot = [&](int j) { return bslot + j >= kBSlots ? bslot + j - kBSlots : bslot + j; };
+            auto bwait = [&](int x) { return warp_wait(&ctl->b_full[x], (bpar >> x) & 1u, abort_flag); };
             for (int v = 0; v < nunits && ok; ++v) {
                 const int ksteps = (min(kMaxSrc, g.n_src - i0) + 7) / 8;  // 8 sources per MMA
                 const uint32_t buf = fills & 1u, fu = fills >> 1;
-                // each source chunk's B halves are built anew, so they are waited for at its first tile
-                if (!warp_wait(&ctl->a_full[buf], fu & 1u, abort_flag) ||
-                    (ct == 0 && !warp_wait(&ctl->b_full[0], bused0 & 1u, abort_flag)) ||
+                const bool first = ct == 0, last = ct == ncols - 1;
+                // the chunk's K-blocks (lo 0, lo 1, then hi 0, hi 1): each built anew per chunk, so
+                // each is waited for at the chunk's first tile right before its MMAs, and released
+                // after its MMAs of the last tile
+                const int x0 = slot(0), x1 = slot(1), x2 = slot(2), x3 = slot(3);
+                if (!warp_wait(&ctl->a_full[buf], fu & 1u, abort_flag) || (first && !bwait(x0)) ||
                     !warp_wait(&ctl->d_empty, (tiles & 1u) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
@@ -971,45 +1055,45 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 const uint32_t dt = tmem + kDCol0;
                 // descriptors advance by the byte offset >> 4 (no carry out of the 14-bit field: B
                 // lies below 256 KB of shared memory)
-                if (ksteps == 8) {
-                    tc_mma_chunk<true>(dt, at, bdesc_lo, kIdesc, tmem + kSfOneA, tmem + kSfOneB, tmem + kBiasACol,
-                                       bias_desc, tmem + kSfBiasA);
+                // lo half, K-block 0, after the bias MMA
+                if (ksteps >= 4) {
+                    tc_mma_quad<true>(dt, at, bdesc0 + (uint64_t)((x0 * kKBlock) >> 4), kIdesc, tmem + kSfOneA,
+                                      tmem + kSfOneB, tmem + kBiasACol, bias_desc, tmem + kSfBiasA);
                 } else {
                     tc_mma_warp(dt, tmem + kBiasACol, bias_desc, kIdesc, tmem + kSfBiasA, tmem + kSfOneB, 0u);
-#pragma unroll
-                    for (int s = 0; s < 7; ++s) {
-                        if (s < ksteps)
-                            tc_mma_warp(dt, at + s * 8,
-                                        bdesc_lo + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
-                                        tmem + kSfOneA, tmem + kSfOneB, 1u);
-                    }
+                    kblock(0, ksteps, at, dt, x0, tmem + kSfOneB);
                 }
-                if (ct == ncols - 1) {
-                    tc_commit_warp(&ctl->b_empty[0]);  // the lo half is free for the next item
-                    ++bused0;
+                if (last) tc_commit_warp(&ctl->b_empty[x0]);
+                // lo half, K-block 1
+                if (first && !bwait(x1)) {
+                    tc_commit_warp(&ctl->d_full);  // the epilogue still sees this pass complete
+                    ok = false;
+                    break;
                 }
+                kblock(1, ksteps, at, dt, x1, tmem + kSfOneB);
+                if (last) tc_commit_warp(&ctl->b_empty[x1]);
                 if (hi) {
-                    if (ct == 0 && !warp_wait(&ctl->b_full[1], bused1 & 1u, abort_flag)) {
-                        tc_commit_warp(&ctl->d_full);  // the epilogue still sees this pass complete
+                    // hi half (block scale 2^10), K-blocks 0 and 1
+                    if (first && !bwait(x2)) {
+                        tc_commit_warp(&ctl->d_full);
                         ok = false;
                         break;
                     }
-                    if (ksteps == 8) {
-                        tc_mma_chunk<false>(dt, at, bdesc_hi, kIdesc, tmem + kSfOneA, tmem + kSfHiB, 0u, 0ull, 0u);
-                    } else {
-#pragma unroll
-                        for (int s = 0; s < 7; ++s) {
-                            if (s < ksteps)
-                                tc_mma_warp(dt, at + s * 8,
-                                            bdesc_hi + (uint64_t)(((s >> 2) * kKBlock + (s & 3) * 32) >> 4), kIdesc,
-                                            tmem + kSfOneA, tmem + kSfHiB, 1u);
-                        }
+                    kblock(0, ksteps, at, dt, x2, tmem + kSfHiB);
+                    if (last) tc_commit_warp(&ctl->b_empty[x2]);
+                    if (first && !bwait(x3)) {
+                        tc_commit_warp(&ctl->d_full);
+                        ok = false;
+                        break;
                     }
+                    kblock(1, ksteps, at, dt, x3, tmem + kSfHiB);
                 }
                 tc_commit_warp(&ctl->d_full);
-                if (hi && ct == ncols - 1) {
-                    tc_commit_warp(&ctl->b_empty[1]);  // the hi half is free for the next item
-                    ++bused1;
+                if (last) {
+                    if (hi) tc_commit_warp(&ctl->b_empty[x3]);
+                    // the chunk's units are consumed: flip their slots' parities, move the ring on
+                    bpar ^= (1u << x0) | (1u << x1) | (hi ? (1u << x2) | (1u << x3) : 0u);
+                    bslot = slot(hi ? 4 : 2);
                 }
                 ++tiles;
                 ++fills;
