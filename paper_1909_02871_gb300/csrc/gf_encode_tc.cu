@@ -26,7 +26,7 @@
 //     of packets 32..63, x N = 256 columns): K-major, 128-byte swizzled, in
 //     K-blocks of 32 sources (32 KB each: lo K-blocks 0 and 1, then hi
 //     K-blocks 0 and 1 per 64-source chunk), built from a per-CTA table of
-//     the coefficients' unit images into a ring of five K-block buffers in
+//     the coefficients' unit images into a ring of six K-block buffers in
 //     shared memory.  The MMAs over the hi half reuse the same A columns and
 //     take block scale 2^10 for B (UE8M0 137);
 //   D (128 lanes x 256 FP32 columns): one pass of 17 MMAs (N = 256) covers
@@ -49,11 +49,11 @@
 // concurrently: 4 warps publish the next item in a two-entry ring (and start
 // its first source tiles and its coefficients on their way into L2), then
 // build its B K-blocks, each into the next slot of the K-block ring: a pass
-// reads at most four, so the next item's first K-block is built while the
-// current item still runs, and each later one as soon as the MMAs of the
+// reads at most four, so the next item's first two K-blocks are built while
+// the current item still runs, and each later one as soon as the MMAs of the
 // current item's last pass are done with the slot it takes over (a commit
 // after each K-block's MMAs of a chunk's last tile); 8 producer warps stage
-// their source rows in shared memory with cp.async two tiles ahead and fill
+// their source rows in shared memory with cp.async a tile ahead and fill
 // A (double-buffered in TMEM, via a 1 KB bit spread computed in registers);
 // 1 warp issues the MMAs (converged, one elected lane issues each group of
 // four from one asm statement; an MMA's issue holds the warp until the
@@ -90,7 +90,7 @@ constexpr int kDN = 256;            // MMA N: accumulator columns per pass (32 p
 constexpr int kMaxSrc = 64;         // sources per chunk (A: 64 TMEM columns, B half: two 32 KB K-blocks)
 constexpr int kSrcPerProducer = kMaxSrc * 4 / kProducerWarps;  // sources of a chunk per producer warp
 constexpr int kRowGroups = kSrcPerProducer / 4;  // a staging copy covers 4 rows (8 lanes each)
-constexpr int kStages = 3;          // source staging depth (tiles) per producer warp
+constexpr int kStages = 2;          // source staging depth (tiles) per producer warp
 constexpr int kStageRow = 40;       // a staged row: the 36 aligned bytes that cover 32 positions, padded
 constexpr int kStageBytes = kSrcPerProducer * kStageRow;  // the warp's sources x 32 byte positions
 constexpr int kBThreads = kBWarps * 32;
@@ -115,8 +115,11 @@ constexpr long long kSentinel = -1;
 
 // shared memory layout (dynamic, 1024-aligned base)
 constexpr int kKBlock = kDN * 128;          // one K-block of B: 256 rows x 128 bytes (32 sources)
-constexpr int kBSlots = 5;                  // K-block buffers in a ring (a pass reads up to 4)
-constexpr int kBiasBBytes = kKBlock;        // 32 KB: rank-1 bias operand (element 0 of every row = 1.0)
+constexpr int kBSlots = 6;                  // K-block buffers in a ring (a pass reads up to 4)
+// rank-1 bias operand B: 256 rows x 64 E2M1 values, unswizzled (8 KB); every 16-byte chunk of
+// every row holds 1.0 in its first element, so its content is the same under any arrangement
+// of rows and chunks (the bias A column has 1.0 in element 0 only: each product is 1.0)
+constexpr int kBiasBBytes = kDN * 32;
 // The unit images of every coefficient of GF(256), GF(16), GF(4), GF(2): 8
 // bytes per coefficient (entry base(n) + c), from which block_row builds
 // the rows of its 8x8 block
@@ -337,11 +340,19 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), descriptor version 1.
+// 1024 bytes apart (SBO), descriptor version 1.  bias_desc: the same for the
+// unswizzled bias operand (8 x 16-byte core matrices, 128 bytes apart along K,
+// 256 bytes apart along N): every read stays inside its 8 KB.
 __device__ __forceinline__ uint64_t b_desc(uint32_t saddr)
 {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ uint64_t bias_desc_of(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46);
 }
 
 // Instruction descriptor, kind::mxf4 block-scaled: A = B = E2M1 (format 1),
@@ -614,12 +625,9 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         }
         tab[e] = Z;
     }
-    // bias operand: K-element 0 of every row is 1.0 (logical 16-byte chunk 0, byte 0)
-    for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x) {
-        const int n = e >> 3, phys = e & 7;
-        const uint32_t first = ((phys ^ (n & 7)) == 0) ? kOne : 0u;
-        *reinterpret_cast<uint4 *>(bias_b + 16 * e) = make_uint4(first, 0u, 0u, 0u);
-    }
+    // bias operand: 1.0 in the first element of every 16-byte chunk
+    for (int e = tid; e < kBiasBBytes / 16; e += blockDim.x)
+        *reinterpret_cast<uint4 *>(bias_b + 16 * e) = make_uint4(kOne, 0u, 0u, 0u);
     if (tid == 0) {
         mbar_init(&ctl->d_full, 1);
         mbar_init(&ctl->d_empty, kEpilogueWarps);
@@ -1003,7 +1011,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
         // fill being consumed
         int bslot = 0;
         uint32_t bpar = 0;
-        const uint64_t bias_desc = b_desc(smem_u32(bias_b));
+        const uint64_t bias_desc = bias_desc_of(smem_u32(bias_b));
         const uint64_t bdesc0 = b_desc(smem_u32(Bs));  // slot x: + x * (K-block >> 4)
         for (uint32_t seq = 0;; ++seq) {
             const uint32_t e = seq & 1u, use = seq >> 1;
