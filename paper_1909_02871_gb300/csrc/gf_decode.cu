@@ -42,6 +42,7 @@
 namespace gf {
 
 constexpr int kDecThreads = 1024;
+constexpr int kDecSmallThreads = 256, kDecSmallN = 64;
 constexpr int kDecBatch = 4;  // arriving rows eliminated against the stored rows together
 
 struct alignas(16) DecMap {
@@ -77,7 +78,7 @@ __device__ __forceinline__ void eliminate_batch(uint32_t *cur, const uint32_t *r
     uint32_t acc[kDecBatch][2];
 #pragma unroll
     for (int b = 0; b < kDecBatch; ++b) acc[b][0] = acc[b][1] = 0u;
-    for (int t = warp; t < rank; t += kDecThreads / 32) {
+    for (int t = warp; t < rank; t += blockDim.x / 32) {
         uint32_t f[kDecBatch];
         uint32_t any = 0u;
 #pragma unroll
@@ -139,8 +140,8 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
     const uint8_t *rowsb = reinterpret_cast<const uint8_t *>(rows);
 
     for (uint32_t c = tid; c < q; c += blockDim.x) {
-        tab[c].m = make_bytemap(n, c);
-        invt[c] = (uint8_t)finv(n, c);
+        tab[c].m = g_field_tables.map[table_base(n) + c];
+        invt[c] = (uint8_t)g_field_tables.inv[table_base(n) + c];
     }
     for (int i = tid; i < N; i += blockDim.x) pivrow[i] = -1;
     if (tid == 0) {
@@ -186,63 +187,114 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         // 4. Gauss-Jordan within the batch, in arrival order: each new pivot row is normalised and
         //    its pivot column eliminated from every other batch row at once (the earlier pivot
         //    rows stay reduced, the later rows arrive at their turn already reduced)
-        for (int b = 0; b < nb; ++b) {
-            // 4a. pivot: first nonzero coefficient of row b (warp 0, ballot over words); the
-            //     other batch rows' values in that column are snapshotted with it
+        if (nw_r <= 32) {
+            // rows of at most 32 words: warp 0 alone, lane j holding word j of every batch row in
+            // registers (no block barrier per row); the same order and rules as below
             if (warp == 0) {
-                const uint32_t *row = cur + b * nw;
-                int piv = -1;
+                uint32_t c[kDecBatch];
+#pragma unroll
+                for (int o = 0; o < kDecBatch; ++o) c[o] = (o < nb && lane < nw_r) ? cur[o * nw + lane] : 0u;
+                int rk = rank, kn = 0, used = s_used;
                 const int ncw = (N + 3) / 4;
-                for (int base = 0; base < ncw && piv < 0; base += 32) {
-                    const int j = base + lane;
-                    uint32_t v = 0;
-                    if (j < ncw) {
-                        v = row[j];
-                        const int valid = N - 4 * j;  // bytes of this word inside [0, N)
-                        if (valid < 4) v &= (1u << (8 * valid)) - 1u;
+                // coefficient bytes of the lane's word (columns < N)
+                const uint32_t cmask = lane < ncw ? (N - 4 * lane >= 4 ? 0xFFFFFFFFu : (1u << (8 * (N - 4 * lane))) - 1u) : 0u;
+#pragma unroll
+                for (int b = 0; b < kDecBatch; ++b) {
+                    if (b >= nb || rk >= N) break;
+                    used = r0 + b + 1;
+                    const uint32_t ball = __ballot_sync(0xffffffffu, (c[b] & cmask) != 0u);
+                    if (!ball) continue;  // no pivot: the row is not innovative and is dropped
+                    const int src = __ffs(ball) - 1;
+                    const uint32_t vw = __shfl_sync(0xffffffffu, c[b] & cmask, src);
+                    const int byte = (__ffs(vw) - 1) >> 3;
+                    const int piv = 4 * src + byte;
+                    const uint32_t pv = (vw >> (8 * byte)) & 0xFFu;
+                    // the other rows' values in the pivot column, before anything changes
+                    uint32_t gv[kDecBatch];
+#pragma unroll
+                    for (int o = 0; o < kDecBatch; ++o)
+                        gv[o] = (__shfl_sync(0xffffffffu, c[o], src) >> (8 * byte)) & 0xFFu;
+                    c[b] = apply_word(tab[invt[pv]].m, c[b]);
+                    const Sel sel = make_sel(c[b]);
+#pragma unroll
+                    for (int o = 0; o < kDecBatch; ++o)
+                        if (o != b && o < nb && gv[o]) c[o] ^= apply(tab[gv[o]].m, sel);
+                    if (lane == 0) {
+                        s_newb[kn] = b;
+                        s_newc[kn] = piv;
                     }
-                    const uint32_t ball = __ballot_sync(0xffffffffu, v != 0);
-                    if (ball) {
-                        const int src = __ffs(ball) - 1;
-                        const uint32_t vw = __shfl_sync(0xffffffffu, v, src);
-                        piv = 4 * (base + src) + (__ffs(vw) - 1) / 8;
-                    }
+                    ++kn;
+                    ++rk;
                 }
+#pragma unroll
+                for (int o = 0; o < kDecBatch; ++o)
+                    if (o < nb && lane < nw_r) cur[o * nw + lane] = c[o];
                 if (lane == 0) {
-                    s_pivot = piv;
-                    if (piv >= 0) s_inv = invt[curb[b * W + piv]];
-                    s_used = r0 + b + 1;
+                    s_knew = kn;
+                    s_rank = rk;
+                    s_used = used;
                 }
-                if (piv >= 0 && lane < nb) s_g[lane] = lane != b ? curb[lane * W + piv] : 0;
             }
             __syncthreads();
-            const int piv = s_pivot;
-            // 4b. normalise row b and eliminate its pivot column from the other batch rows (a
-            //     thread owns a word column of every batch row); a row without a pivot is not
-            //     innovative and is dropped
-            if (piv >= 0) {
-                const ByteMap m = tab[s_inv].m;
-                for (int j = tid; j < nw_r; j += blockDim.x) {
-                    const uint32_t pv = apply_word(m, cur[b * nw + j]);
-                    cur[b * nw + j] = pv;
-                    const Sel sel = make_sel(pv);
-#pragma unroll
-                    for (int o = 0; o < kDecBatch; ++o) {
-                        if (o >= nb) break;
-                        const uint32_t go = s_g[o];
-                        if (o != b && go) cur[o * nw + j] ^= apply(tab[go].m, sel);
+        } else {
+            for (int b = 0; b < nb; ++b) {
+                // 4a. pivot: first nonzero coefficient of row b (warp 0, ballot over words); the
+                //     other batch rows' values in that column are snapshotted with it
+                if (warp == 0) {
+                    const uint32_t *row = cur + b * nw;
+                    int piv = -1;
+                    const int ncw = (N + 3) / 4;
+                    for (int base = 0; base < ncw && piv < 0; base += 32) {
+                        const int j = base + lane;
+                        uint32_t v = 0;
+                        if (j < ncw) {
+                            v = row[j];
+                            const int valid = N - 4 * j;  // bytes of this word inside [0, N)
+                            if (valid < 4) v &= (1u << (8 * valid)) - 1u;
+                        }
+                        const uint32_t ball = __ballot_sync(0xffffffffu, v != 0);
+                        if (ball) {
+                            const int src = __ffs(ball) - 1;
+                            const uint32_t vw = __shfl_sync(0xffffffffu, v, src);
+                            piv = 4 * (base + src) + (__ffs(vw) - 1) / 8;
+                        }
+                    }
+                    if (lane == 0) {
+                        s_pivot = piv;
+                        if (piv >= 0) s_inv = invt[curb[b * W + piv]];
+                        s_used = r0 + b + 1;
+                    }
+                    if (piv >= 0 && lane < nb) s_g[lane] = lane != b ? curb[lane * W + piv] : 0;
+                }
+                __syncthreads();
+                const int piv = s_pivot;
+                // 4b. normalise row b and eliminate its pivot column from the other batch rows (a
+                //     thread owns a word column of every batch row); a row without a pivot is not
+                //     innovative and is dropped
+                if (piv >= 0) {
+                    const ByteMap m = tab[s_inv].m;
+                    for (int j = tid; j < nw_r; j += blockDim.x) {
+                        const uint32_t pv = apply_word(m, cur[b * nw + j]);
+                        cur[b * nw + j] = pv;
+                        const Sel sel = make_sel(pv);
+    #pragma unroll
+                        for (int o = 0; o < kDecBatch; ++o) {
+                            if (o >= nb) break;
+                            const uint32_t go = s_g[o];
+                            if (o != b && go) cur[o * nw + j] ^= apply(tab[go].m, sel);
+                        }
                     }
                 }
+                if (tid == 0 && piv >= 0) {
+                    const int knew = s_knew;
+                    s_newb[knew] = b;
+                    s_newc[knew] = piv;
+                    s_knew = knew + 1;
+                    s_rank = s_rank + 1;
+                }
+                __syncthreads();  // also keeps the pivot shared state of this row until every thread has read it
+                if (s_rank >= N) break;
             }
-            if (tid == 0 && piv >= 0) {
-                const int knew = s_knew;
-                s_newb[knew] = b;
-                s_newc[knew] = piv;
-                s_knew = knew + 1;
-                s_rank = s_rank + 1;
-            }
-            __syncthreads();  // also keeps the pivot shared state of this row until every thread has read it
-            if (s_rank >= N) break;
         }
         const int knew = s_knew;
         // 5. back-substitution of the batch's pivots into the stored rows, one sweep: G first
@@ -256,8 +308,8 @@ __global__ void __launch_bounds__(kDecThreads) decode_coef_kernel(const DecGen *
         //    computed once) and walks a share of the stored rows
         if (knew > 0 && rank > 0) {
             const int ng = nw_r / 4;                               // 16-byte word groups
-            const int per = max(1, kDecThreads / max(ng, 1));      // threads per group
-            const int groups = kDecThreads / per;
+            const int per = max(1, (int)blockDim.x / max(ng, 1));  // threads per group
+            const int groups = (int)blockDim.x / per;
             const int g_start = tid % groups, part = tid / groups;
             for (int gq = g_start; gq < ng && part < per; gq += groups) {
                 const int j = 4 * gq;
@@ -473,7 +525,7 @@ int launch_decode_coef(const DecodeWork &w, const DecGen *d_gens, cudaStream_t s
     if (w.n_coef == 0) return GF_OK;
     const int st = configure_decode_coef();
     if (st != GF_OK) return st;
-    decode_coef_kernel<<<(unsigned)w.n_coef, kDecThreads, w.smem, stream>>>(d_gens);
+    decode_coef_kernel<<<(unsigned)w.n_coef, (unsigned)w.coef_threads, w.smem, stream>>>(d_gens);
     return cuda_status(cudaGetLastError());
 }
 
@@ -523,6 +575,11 @@ size_t stage_decode(DecodeWork &w, char *host, char *dev_base, size_t off, WorkC
         return (double)a.N * a.N * (a.N + a.R) > (double)b.N * b.N * (b.N + b.R);
     });
     w.n_coef = (int)order.size();
+    // small generations: a 256-thread CTA (a few words per row operation; fewer warps make the
+    // barriers between the row steps cheaper)
+    int max_n = 0;
+    for (const DecGen &g : order) max_n = std::max(max_n, g.N);
+    w.coef_threads = max_n <= kDecSmallN ? kDecSmallThreads : kDecThreads;
     const size_t gb = order.size() * sizeof(DecGen);
     if (gb) memcpy(host + off, order.data(), gb);
     w.d_gens = reinterpret_cast<DecGen *>(dev_base + off);

@@ -60,6 +60,7 @@ struct DecodeWork {
     size_t x_bytes = 0, grow_bytes = 0, smem = 0;
     DecGen *d_gens = nullptr;
     int n_coef = 0;  // generations of decode_coef_kernel (the others are blocked)
+    int coef_threads = 1024;  // its CTA size: 256 when every such generation has at most 64 sources
     // blocked generations and, per step, the batches of their two row products
     std::vector<BlkGen> blk;
     std::vector<std::vector<EncodeBatch>> prod1, prod2;

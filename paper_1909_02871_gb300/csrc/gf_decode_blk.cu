@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kGjThreads) blk_gj_kernel(const BlkGen *__rest
         return;
     }
     for (uint32_t c = tid; c < q; c += blockDim.x) {
-        tab[c].m = make_bytemap(n, c);
-        invt[c] = (uint8_t)finv(n, c);
+        tab[c].m = g_field_tables.map[table_base(n) + c];
+        invt[c] = (uint8_t)g_field_tables.inv[table_base(n) + c];
     }
     // live words: rows so far carry transform entries only up to column N + r0 + nb - 1
     const int nw_r = min(nw, (N + r0 + nb + 15) / 16 * 4);

@@ -187,14 +187,7 @@ encode_table_kernel(const EncGen *__restrict__ gens, const long long *__restrict
                     long long total, WorkCounter *ctr)
 {
     __shared__ SmemMap tab[kTableEntries];
-    for (int e = threadIdx.x; e < kTableEntries; e += blockDim.x) {
-        int n, c;
-        if (e < 2) { n = 1; c = e; }
-        else if (e < 6) { n = 2; c = e - 2; }
-        else if (e < 22) { n = 4; c = e - 6; }
-        else { n = 8; c = e - 22; }
-        tab[e].m = make_bytemap(n, (uint32_t)c);
-    }
+    for (int e = threadIdx.x; e < kTableEntries; e += blockDim.x) tab[e].m = g_field_tables.map[e];
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
