@@ -80,25 +80,28 @@ int choose_path(int field, int n_src, int n_coded, unsigned long long len)
     }
     if (!bitsliced_available() || n_src <= 0 || n_coded <= 0 || len == 0) return GF_PATH_TABLE;
     // Cost model in SM clocks per generation per SM, fitted to the tuner's
-    // own timings of 192 shapes on a GB300 (GF(2) and GF(256); N 8..255, K
-    // 8..64, len 128..4096): a tensor-core pass (128 bytes x up to 64 coded
-    // packets x up to 64 sources) costs about 3900 clocks of handshakes and
-    // B building plus about 100 per MMA issued (the bias MMA and one per 8
-    // sources, twice for more than 32 coded packets); the table path costs
-    // about 50 clocks per source and 90 more for every 128-byte x 8-packet
-    // tile (GF(2), a plain XOR, about 0.77 of the per-source cost).  With
-    // these constants AUTO picks the tuner's choice on 164 of the 192 shapes
-    // and is 5 % slower than it on average.
+    // own timings of 288 shapes on a GB300 (GF(2) and GF(256); N 8..255, K
+    // 8..64, len 128..4096, 304-608 generations): a tensor-core pass (128
+    // bytes x up to 64 coded packets x up to 64 sources) costs about 2300
+    // clocks of handshakes plus about 30 per MMA issued (the bias MMA and one
+    // per 8 sources, twice for more than 32 coded packets), and every 32 KB
+    // K-block of coefficient matrices built about 300; the table path costs
+    // about 50 clocks per source for every 128-byte x 8-packet tile (GF(2),
+    // a plain XOR, about 0.55 of that).  With these constants AUTO picks the
+    // tuner's choice on 251 of the 288 shapes and is 4 % slower than it on
+    // average (the constants fitted to the kernel before its K-block ring and
+    // batched MMA issue: 239 shapes, 7 %).
     const int chunks = (n_src + 63) / 64, items = (n_coded + 63) / 64;
     const double tiles = std::ceil((double)len / 128.0);
-    double mmas = 0.0;
+    double mmas = 0.0, kblocks = 0.0;
     for (int it = 0; it < items; ++it) {
         const int halves = std::min(n_coded - 64 * it, 64) > 32 ? 2 : 1;
         for (int c = 0; c < chunks; ++c) mmas += 1 + halves * ((std::min(n_src - 64 * c, 64) + 7) / 8);
+        kblocks += 2.0 * halves * chunks;
     }
-    const double bits = tiles * (3900.0 * chunks * items + 100.0 * mmas);
+    const double bits = tiles * (2300.0 * chunks * items + 30.0 * mmas) + 300.0 * kblocks;
     const double ttiles = tiles * std::ceil(n_coded / 8.0);
-    const double table = ttiles * (50.0 * n_src * (field == 1 ? 0.77 : 1.0) + 90.0);
+    const double table = ttiles * (50.0 * n_src * (field == 1 ? 0.55 : 1.0));
     if (bits < table) return GF_PATH_BITSLICED;
     return GF_PATH_TABLE;
 }
