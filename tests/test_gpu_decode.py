@@ -108,6 +108,29 @@ def test_uneven_batch_one_call():
         assert r[2] == ge.n_src and np.array_equal(r[0], ge.src)
 
 
+@pytest.mark.parametrize("field", [2, 8])
+@pytest.mark.parametrize("N", [40, 63])
+def test_rows_crossing_the_register_settling_width(field, N):
+    """Rows of at most 32 words (N + rows so far <= 128 bytes) are settled by
+    one warp in registers, wider ones block-wide: zero and repeated rows
+    first keep the rank low while the rows grow past 128 bytes, so one
+    generation takes both forms, in one launch with a generation that takes
+    only the first."""
+    g = synth.choice(72, field, N)
+    src = synth.random_bytes(g, (N, 40))
+    base = synth.coefficients(g, field, (6, N), nonzero=True)
+    rows = [np.zeros((20, N), np.uint8), base[g.integers(0, 6, 70)],
+            synth.coefficients(g, field, (N + 10, N), nonzero=False)]
+    coef = np.ascontiguousarray(np.concatenate(rows))
+    small = synth.coefficients(g, field, (12, 10), nonzero=True)
+    items = [(field, coef, oracle.encode(field, src, coef)),
+             (field, small, oracle.encode(field, synth.random_bytes(g, (10, 40)), small))]
+    got = _decode(items)
+    for (fld, c, payload), r in zip(items, got):
+        _check(fld, c, payload, r)
+    assert got[0][2] == N and np.array_equal(got[0][0], src)
+
+
 @pytest.mark.parametrize("field", [1, 8])
 @pytest.mark.parametrize("N,R", [(255, 300), (400, 420), (400, 1700)])
 def test_large_generations(field, N, R):
