@@ -324,14 +324,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         : "memory");
 }
 
-// 32 lanes x 32 columns of 16-bit values, two adjacent columns per register
-__device__ __forceinline__ void tmem_ld16_pack(uint32_t taddr, uint32_t (&v)[16])
+// 32 lanes x 64 columns, low 16 bits of each, two columns per register
+// (register i: columns 2i, 2i+1): columns 0..31 into v, 32..63 into u
+__device__ __forceinline__ void tmem_ld32_pack(uint32_t taddr, uint32_t (&v)[16], uint32_t (&u)[16])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.pack::16b.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-        "%13, %14, %15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.pack::16b.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
         : "r"(taddr)
         : "memory");
 }
@@ -900,8 +903,7 @@ encode_bitsliced_kernel(const EncGen *__restrict__ gens, const long long *__rest
                 if (poller && lane == 0) mbar_arrive(&ctl->a_empty[tiles & 1u]);
                 const uint32_t dcol = tmem + ((uint32_t)(quarter * 32) << 16) + kDCol0 + oct * 64;
                 uint32_t va[16], vb[16];
-                tmem_ld16_pack(dcol, va);
-                tmem_ld16_pack(dcol + 32, vb);
+                tmem_ld32_pack(dcol, va, vb);  // one load for the warp's 64 columns
                 tmem_wait_ld();
                 tc_fence_before();
                 __syncwarp();
