@@ -127,22 +127,22 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
 #pragma unroll
         for (int i = 0; i < WPT; ++i) acc[k][i] = 0u;
 
-    for (int i = 0; i < N; ++i) {
-        // the tile's coefficients of source i first (the same for every lane): a source
-        // they all leave out is not loaded at all (sparse coding matrices, e.g. the transform
-        // of a decode whose received packets are mostly sources sent uncoded)
-        uint32_t c4[KPT / 4];  // four coefficients per register
+    // the tile's coefficients of source i, four per register (the same for every lane)
+    auto load_coef = [&](int i, uint32_t (&c4)[KPT / 4]) {
 #pragma unroll
         for (int q = 0; q < KPT / 4; ++q) c4[q] = 0u;
 #pragma unroll
         for (int k = 0; k < KPT; ++k)
             if (k < kn) c4[k >> 2] |= (uint32_t)__ldg(coefk + (size_t)k * ld + i) << (8 * (k & 3));
+    };
+    auto nonzero = [](const uint32_t (&c4)[KPT / 4]) {
         uint32_t any = 0u;
 #pragma unroll
         for (int q = 0; q < KPT / 4; ++q) any |= c4[q];
-        if (any == 0u) continue;
-        uint32_t w[WPT];
-        load_words<WPT>(g.src + (size_t)i * len, col, len, w);
+        return any != 0u;
+    };
+    // acc[k] ^= c_k * (the words w of one source), through the words' prmt selectors
+    auto madd = [&](const uint32_t (&c4)[KPT / 4], const uint32_t (&w)[WPT]) {
         Sel s[WPT];
 #pragma unroll
         for (int j = 0; j < WPT; ++j) s[j] = make_sel(w[j]);
@@ -154,6 +154,48 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
 #pragma unroll
                 for (int j = 0; j < WPT; ++j) acc[k][j] ^= apply(m, s[j]);
             }
+        }
+    };
+
+    if (KPT * WPT <= 32) {
+        // Tiles with registers to spare load ahead: the next source's words and the
+        // coefficients of the one after are on their way while this source is applied (a
+        // source's words wait for its coefficients, so that a source they all leave out --
+        // sparse coding matrices, e.g. the transform of a decode whose received packets are
+        // mostly sources sent uncoded -- is not loaded at all)
+        uint32_t ca[KPT / 4], cb[KPT / 4], w[WPT], wn[WPT];
+        load_coef(0, ca);
+        if (N > 1) load_coef(1, cb);
+        bool za = nonzero(ca);
+        if (za) load_words<WPT>(g.src, col, len, w);
+        for (int i = 0; i < N; ++i) {
+            bool zb = false;
+            if (i + 1 < N) {
+                zb = nonzero(cb);
+                if (zb) load_words<WPT>(g.src + (size_t)(i + 1) * len, col, len, wn);
+            }
+            uint32_t cc[KPT / 4];
+            if (i + 2 < N) load_coef(i + 2, cc);
+            if (za) madd(ca, w);
+#pragma unroll
+            for (int q = 0; q < KPT / 4; ++q) {
+                ca[q] = cb[q];
+                cb[q] = i + 2 < N ? cc[q] : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < WPT; ++j) w[j] = wn[j];
+            za = zb;
+        }
+    } else {
+        for (int i = 0; i < N; ++i) {
+            // the tile's coefficients of source i first: a source they all leave out is not
+            // loaded at all (sparse coding matrices, as above)
+            uint32_t c4[KPT / 4];
+            load_coef(i, c4);
+            if (!nonzero(c4)) continue;
+            uint32_t w[WPT];
+            load_words<WPT>(g.src + (size_t)i * len, col, len, w);
+            madd(c4, w);
         }
     }
 #pragma unroll
