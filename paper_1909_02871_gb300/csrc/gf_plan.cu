@@ -68,7 +68,9 @@ int choose_table_variant(int field, int n_src, int n_coded, unsigned long long l
     (void)n_src;
     if (len <= 160) return 1;             // 128-byte column tiles
     if (len <= 320) return 2;             // 256-byte column tiles
-    return n_coded <= 8 ? 3 : 0;          // 512-byte column tiles
+    // 512-byte column tiles: 8 packets per tile (the shape that loads a source ahead) up to 16
+    // coded packets -- the tuner's choice on every Fig. 1 point from 512 B up -- else 16
+    return n_coded <= 16 ? 3 : 0;
 }
 
 int choose_path(int field, int n_src, int n_coded, unsigned long long len)
