@@ -163,11 +163,14 @@ __device__ __forceinline__ void table_tile(const SmemMap *tab, const EncGen &g, 
         // source's words wait for its coefficients, so that a source they all leave out --
         // sparse coding matrices, e.g. the transform of a decode whose received packets are
         // mostly sources sent uncoded -- is not loaded at all)
-        uint32_t ca[KPT / 4], cb[KPT / 4], w[WPT], wn[WPT];
-        load_coef(0, ca);
+        uint32_t ca[KPT / 4] = {}, cb[KPT / 4] = {}, w[WPT] = {}, wn[WPT] = {};
+        bool za = false;  // a generation without sources reads nothing (its outputs are zero)
+        if (N > 0) {
+            load_coef(0, ca);
+            za = nonzero(ca);
+            if (za) load_words<WPT>(g.src, col, len, w);
+        }
         if (N > 1) load_coef(1, cb);
-        bool za = nonzero(ca);
-        if (za) load_words<WPT>(g.src, col, len, w);
         for (int i = 0; i < N; ++i) {
             bool zb = false;
             if (i + 1 < N) {
