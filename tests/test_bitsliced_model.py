@@ -164,11 +164,12 @@ def test_encode_with_two_packets_per_column(n):
 def test_permuted_bit_order_of_the_kernel():
     """The kernel orders the 8 bits of a source byte as (0, 4, 1, 5, 2, 6, 3, 7)
     along K, on both sides: the source side spreads a byte with two halving
-    steps, the coefficient side builds row r of a block from the unit images
-    p_j (the image of the unit byte with bit j set) with a shift and two
-    masks.  Restated here bit for bit, the nibble-wise dot product of row r
-    with the spread byte a has the parity of bit r of c*a, for every
-    coefficient, byte and field."""
+    steps, the coefficient side keeps the unit images p_j (the image of the
+    unit byte with bit j set) as two nibble planes (nibble t of Z.x / Z.y is
+    the low / high nibble of p_(t%2*4 + t/2)) and builds row r of a block
+    with one shift and one mask.  Restated here bit for bit, the nibble-wise
+    dot product of row r with the spread byte a has the parity of bit r of
+    c*a, for every coefficient, byte and field."""
     order = [0, 4, 1, 5, 2, 6, 3, 7]
 
     def spread(b):
@@ -176,8 +177,16 @@ def test_permuted_bit_order_of_the_kernel():
         x = (x | (x << 7)) & 0x11111111
         return (x << 1) & 0xFFFFFFFF
 
-    def block_row(px, py, r):
-        return (((px >> r) & 0x01010101) | (((py >> r) & 0x01010101) << 4)) << 1
+    def planes(imgs):
+        zx = zy = 0
+        for t in range(8):
+            p = imgs[(t & 1) * 4 + (t >> 1)]
+            zx |= (p & 0xF) << (4 * t)
+            zy |= (p >> 4) << (4 * t)
+        return zx, zy
+
+    def block_row(zx, zy, r):
+        return (((zx if r < 4 else zy) >> (r & 3)) & 0x11111111) << 1
 
     for b in range(256):
         w = spread(b)
@@ -186,12 +195,33 @@ def test_permuted_bit_order_of_the_kernel():
     for n in FIELDS:
         for c in range(1 << n):
             imgs = [int(oracle.region_mul(n, np.array([1 << j], np.uint8), c)[0]) for j in range(8)]
-            px = imgs[0] | imgs[1] << 8 | imgs[2] << 16 | imgs[3] << 24
-            py = imgs[4] | imgs[5] << 8 | imgs[6] << 16 | imgs[7] << 24
-            rows = [block_row(px, py, r) for r in range(8)]
+            zx, zy = planes(imgs)
+            rows = [block_row(zx, zy, r) for r in range(8)]
             for a in range(256):
                 wa = spread(a)
                 prod = int(oracle.region_mul(n, np.array([a], np.uint8), c)[0])
                 for r in range(8):
                     dot = sum(((rows[r] >> (4 * k)) & 0xF) * ((wa >> (4 * k)) & 0xF) for k in range(8)) // 4
                     assert dot % 2 == (prod >> r) & 1, (n, c, a, r)
+
+
+def test_quad_byte_transpose_of_the_epilogue():
+    """The epilogue stores rows of 4-byte aligned words after a byte
+    transpose within each quad of lanes: lane j of a quad starts with byte t
+    of its word = packet t at position j, exchanges with lane j^1 (byte
+    selectors 0x6240 / 0x3715 for even / odd lanes) and then with lane j^2
+    (0x5410 / 0x3276), and ends with byte i = packet j at position i.
+    Restated with prmt's byte selection, for random words."""
+    def prmt(a, b, sel):
+        pool = [(a >> (8 * i)) & 0xFF for i in range(4)] + [(b >> (8 * i)) & 0xFF for i in range(4)]
+        return sum(pool[(sel >> (4 * i)) & 7] << (8 * i) for i in range(4))
+
+    g = np.random.default_rng(5)
+    for _ in range(200):
+        m = g.integers(0, 256, (4, 32))                       # m[packet][position]
+        w = [sum(int(m[t][j]) << (8 * t) for t in range(4)) for j in range(32)]
+        z = [prmt(w[j], w[j ^ 1], 0x3715 if j & 1 else 0x6240) for j in range(32)]
+        v = [prmt(z[j], z[j ^ 2], 0x3276 if j & 2 else 0x5410) for j in range(32)]
+        for j in range(32):
+            q, jj = j >> 2, j & 3
+            assert v[j] == sum(int(m[jj][4 * q + i]) << (8 * i) for i in range(4))
